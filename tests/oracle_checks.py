@@ -1,0 +1,394 @@
+"""Checks that pin the CPU oracle to what the paper and the mathematics fix.
+
+Every check takes the oracle object (the module, or a build of it with a planted
+mistake) and raises AssertionError when it disagrees.
+
+Each test names the passage it pins.  None of them re-types the oracle's formulas:
+they use closed forms, invariants, library routines (scipy), brute force, or two
+mathematically equivalent evaluations.
+"""
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.optimize
+
+from paper_1412_1498_gb300 import fields
+from tests import obs
+
+L4 = (4, 4, 4, 4)
+
+
+def unit_field(dims):
+    Lx, Ly, Lz, Lt = dims
+    return np.broadcast_to(np.eye(3, dtype=complex), (Lt, Lz, Ly, Lx, 4, 3, 3)).copy()
+
+
+def haar(n, seed):
+    return fields.haar_su3(n, np.random.Generator(np.random.Philox(key=1000 + seed)))
+
+
+# --- Eqs. (1)-(3): F and theta ------------------------------------------------------
+
+def check_unit_field_closed_form(orc, gauge):
+    F, th, F_t, th_t = orc.measure(unit_field((4, 2, 4, 6)), gauge)
+    assert F == 1.0 and th == 0.0
+    assert np.all(F_t == 1.0) and np.all(th_t == 0.0)
+
+
+def check_constant_diagonal_field_closed_form(orc):
+    # U_mu(x) = diag(e^{i p}, e^{i p}, e^{-2ip}) everywhere: Delta = 0 (Eq. 3 telescopes),
+    # F = (2 cos p + cos 2p) / 3 for every mu (Eq. 1).
+    p = 0.37
+    U = unit_field(L4)
+    U[..., :, :, :] = np.diag([np.exp(1j * p), np.exp(1j * p), np.exp(-2j * p)])
+    F, th, _, _ = orc.measure(U)
+    assert abs(F - (2 * np.cos(p) + np.cos(2 * p)) / 3) < 1e-15
+    assert th == 0.0
+
+
+def check_single_link_excitation_closed_form(orc, nu):
+    # Unit field with one link U_nu(y) = W: A(x) = sum [U(x-nu) - U(x)] is non-zero only
+    # at x = y (1 - W) and x = y + nu (W - 1).  theta = 2 |W - W^+ - tr/3|^2 / (Nc V).
+    dims = (4, 4, 6, 4)
+    U = unit_field(dims)
+    W = haar(1, nu)[0]
+    y = (1, 2, 3, 1)  # (t, z, y, x) of the site
+    U[y][nu] = W
+    D = orc.delta(U, orc.LANDAU)
+    M = W - W.conj().T
+    M = M - np.trace(M) / 3 * np.eye(3)
+    yp = list(y)
+    axis = obs.AXIS[nu]
+    yp[axis] = (yp[axis] + 1) % U.shape[axis]
+    assert np.abs(D[y] + M).max() < 1e-15
+    assert np.abs(D[tuple(yp)] - M).max() < 1e-15
+    mask = np.ones(D.shape[:4], bool)
+    mask[y] = mask[tuple(yp)] = False
+    assert np.abs(D[mask]).max() == 0
+    V = np.prod(dims)
+    assert abs(orc.measure(U)[1] - 2 * np.sum(np.abs(M) ** 2) / (3 * V)) < 1e-15
+
+
+def check_delta_properties_and_two_theta_evaluations(orc):
+    U = fields.random_gauge_config(L4, 0.5, 5)
+    D = orc.delta(U)
+    # Delta is anti-Hermitian and traceless; sum_x Delta(x) = 0 by periodicity
+    assert np.abs(D + obs.dag(D)).max() < 1e-14
+    assert np.abs(np.trace(D, axis1=-2, axis2=-1)).max() < 1e-14
+    assert np.abs(D.sum(axis=(0, 1, 2, 3))).max() < 1e-11
+    F, th, _, _ = orc.measure(U)
+    V = np.prod(L4)
+    # theta (Eq. 2) from Delta, and from its Gell-Mann components:
+    # Tr[Delta Delta^+] = 2 sum_a x_a^2 with x_a = Tr[l_a Delta] / (2i)
+    assert abs(th - np.sum(np.abs(D) ** 2) / (3 * V)) < 1e-13 * th
+    xa = np.einsum("aij,...ji->...a", fields.gell_mann(), D) / 2j
+    assert np.abs(xa.imag).max() < 1e-13
+    assert abs(th - 2 * np.sum(xa.real ** 2) / (3 * V)) < 1e-12 * th
+
+
+def check_gradient_identity(orc, gauge):
+    # A gauge transformation g = exp(i c_a l_a) at one site x changes F (Eq. 1) at
+    # first order by dF/dc_a = Tr[l_a Delta(x)] / (2i nd Nc V): Delta is the gradient.
+    dims = (4, 4, 4, 6)
+    nd = 4 if gauge == orc.LANDAU else 3
+    U = fields.random_gauge_config(dims, 0.5, 9)
+    D = orc.delta(U, gauge)
+    l = fields.gell_mann()
+    V = np.prod(dims)
+    site = (3, 1, 2, 0)
+    h = 1e-6
+    for a in (0, 3, 7):
+        vals = []
+        for s in (+1, -1):
+            g = scipy.linalg.expm(1j * s * h * l[a])
+            W = U.copy()
+            for mu in range(4):
+                W[site][mu] = g @ W[site][mu]
+                b = list(site)
+                ax = obs.AXIS[mu]
+                b[ax] = (b[ax] - 1) % U.shape[ax]
+                W[tuple(b)][mu] = W[tuple(b)][mu] @ g.conj().T
+            vals.append(orc.measure(W, gauge)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = (np.trace(l[a] @ D[site]) / (2j * nd * 3 * V)).real
+        assert abs(fd - an) < 1e-9 * max(1.0, abs(an) * V), (a, fd, an)
+
+
+def check_global_rotation_invariance(orc):
+    U = fields.random_gauge_config(L4, 0.5, 2)
+    Om = haar(1, 77)[0]
+    W = Om @ U @ Om.conj().T
+    a, b = orc.measure(U), orc.measure(W)
+    assert abs(a[0] - b[0]) < 1e-14 and abs(a[1] - b[1]) < 1e-13 * a[1]
+
+
+# --- Eqs. (4)-(6): the SU(2) subgroup maximiser ---------------------------------------
+
+def _embed(a, b, i, j):
+    R = np.eye(3, dtype=complex)
+    R[i, i], R[i, j], R[j, i], R[j, j] = a, b, -np.conj(b), np.conj(a)
+    return R
+
+
+def _brute_max(K, i, j):
+    # grid over S^3 (a = q0 + i q1, b = q2 + i q3), refined by a local optimiser
+    def val(q):
+        q = q / np.linalg.norm(q)
+        return np.trace(_embed(q[0] + 1j * q[1], q[2] + 1j * q[3], i, j) @ K).real
+    t = np.linspace(0, np.pi, 13)
+    best, bq = -np.inf, None
+    for t1 in t:
+        for t2 in t:
+            for t3 in np.linspace(0, 2 * np.pi, 25):
+                q = np.array([np.cos(t1), np.sin(t1) * np.cos(t2), np.sin(t1) * np.sin(t2) * np.cos(t3),
+                              np.sin(t1) * np.sin(t2) * np.sin(t3)])
+                v = val(q)
+                if v > best:
+                    best, bq = v, q
+    res = scipy.optimize.minimize(lambda q: -val(q), bq, method="Nelder-Mead",
+                                  options=dict(xatol=1e-12, fatol=1e-14, maxiter=20000))
+    return max(best, -res.fun), res.x / np.linalg.norm(res.x)
+
+
+def check_su2_maximiser_matches_brute_force_on_2x4_lattice(orc):
+    # K(x) of every site of a 2^4 lattice, in-place form of Eq. (5)
+    U = fields.random_gauge_config((2, 2, 2, 2), 0.6, 4)
+    count = 0
+    for t in range(2):
+        for z in range(2):
+            for y in range(2):
+                for x in range(2):
+                    site = (t, z, y, x)
+                    K = np.zeros((3, 3), complex)
+                    for mu in range(4):
+                        b = list(site)
+                        ax = obs.AXIS[mu]
+                        b[ax] = (b[ax] - 1) % 2
+                        K += U[site][mu] + U[tuple(b)][mu].conj().T
+                    for (i, j) in ((0, 1), (0, 2), (1, 2)):
+                        a, bb = orc.su2_maximiser(K, i, j, 1.0)
+                        R = _embed(a, bb, i, j)
+                        got = np.trace(R @ K).real
+                        best, _ = _brute_max(K, i, j)
+                        assert abs(abs(a) ** 2 + abs(bb) ** 2 - 1) < 1e-15
+                        assert got >= best - 1e-9, (site, i, j, got, best)
+                        count += 1
+    assert count == 48
+
+
+def check_su2_maximiser_value_and_degenerate_case(orc):
+    K = np.zeros((3, 3), complex)
+    a, b = orc.su2_maximiser(K, 0, 1, 1.7)
+    assert (a, b) == (1, 0)
+    rng = np.random.default_rng(3)
+    K = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+    for (i, j) in ((0, 1), (0, 2), (1, 2)):
+        a, b = orc.su2_maximiser(K, i, j, 1.0)
+        R = _embed(a, b, i, j)
+        rest = sum(K[k, k].real for k in range(3) if k not in (i, j))
+        # the maximum of Re Tr[R K] is |(alpha, beta)| plus the untouched diagonal;
+        # check it as the largest singular value of the real 4-vector map (independent)
+        M = np.array([[K[i, i].real + K[j, j].real, -K[i, i].imag + K[j, j].imag,
+                       K[j, i].real - K[i, j].real, -K[j, i].imag - K[i, j].imag]])
+        assert abs(np.trace(R @ K).real - rest - np.linalg.norm(M)) < 1e-13
+
+
+def check_overrelaxation_exact_form_is_matrix_power(orc):
+    rng = np.random.default_rng(5)
+    for trial in range(20):
+        K = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        a, b = orc.su2_maximiser(K, 0, 2, 1.0)
+        r = np.array([[a, b], [-np.conj(b), np.conj(a)]])
+        for om in (1.0, 1.3, 1.7, 1.95):
+            ae, be = orc.su2_maximiser(K, 0, 2, om, orc.OR_EXACT)
+            re = np.array([[ae, be], [-np.conj(be), np.conj(ae)]])
+            ref = scipy.linalg.fractional_matrix_power(r, om)
+            assert np.abs(re - ref).max() < 1e-10, (trial, om)
+
+
+def check_overrelaxation_first_order_form(orc):
+    rng = np.random.default_rng(6)
+    for trial in range(20):
+        K = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        a, b = orc.su2_maximiser(K, 1, 2, 1.0)
+        r = np.array([[a, b], [-np.conj(b), np.conj(a)]])
+        a1, b1 = orc.su2_maximiser(K, 1, 2, 1.0, orc.OR_FIRST_ORDER)
+        assert abs(a1 - a) < 1e-15 and abs(b1 - b) < 1e-15
+        om = 1.6
+        af, bf = orc.su2_maximiser(K, 1, 2, om, orc.OR_FIRST_ORDER)
+        rf = np.array([[af, bf], [-np.conj(bf), np.conj(af)]])
+        assert abs(abs(af) ** 2 + abs(bf) ** 2 - 1) < 1e-15
+        assert np.abs(rf @ r - r @ rf).max() < 1e-14          # same rotation axis
+        # rotation angle: first order gives tan(phi') = om sin(phi) / (1 - om + om cos(phi))
+        phi = np.arccos(np.clip(a.real, -1, 1))
+        phi_f = np.arccos(np.clip(af.real, -1, 1))
+        want = np.arctan2(om * np.sin(phi), 1 - om + om * np.cos(phi))
+        assert abs(phi_f - want) < 1e-12
+        # and agrees with the exact power to second order in phi
+        small = scipy.linalg.fractional_matrix_power(r, om)
+        assert np.abs(rf - small).max() < 2 * phi ** 2 + 1e-12
+
+
+# --- Algorithm 1: half-sweeps ---------------------------------------------------------
+
+def check_relaxation_omega1_never_decreases_F(orc, form, gauge):
+    U = fields.random_gauge_config((4, 4, 4, 6), 0.5, 12)
+    F_prev = orc.measure(U, gauge)[0]
+    for k in range(10):
+        orc.or_half_sweep(U, k % 2, 1.0, gauge, form)
+        F = orc.measure(U, gauge)[0]
+        assert F >= F_prev - 1e-15, (k, F, F_prev)
+        F_prev = F
+
+
+def check_sweeps_are_gauge_transformations(orc, gauge):
+    U = fields.random_gauge_config((4, 4, 6, 4), 0.5, 13)
+    P0, R0, L0 = obs.plaquettes(U), obs.rectangles(U), obs.polyakov(U)
+    Lx0 = obs.polyakov(U, 0)
+    for k in range(25):
+        orc.sweep(U, 1.7, gauge, reunit=(k % 20 == 19))
+    assert obs.unitarity_error(U) < 1e-13 and obs.det_error(U) < 1e-13
+    assert np.abs(obs.plaquettes(U) - P0).max() < 1e-12
+    assert np.abs(obs.rectangles(U) - R0).max() < 1e-12
+    assert np.abs(obs.polyakov(U) - L0).max() < 1e-12
+    assert np.abs(obs.polyakov(U, 0) - Lx0).max() < 1e-12
+
+
+def check_half_sweep_touches_only_its_parity(orc):
+    # Algorithm 1 updates the sites of one parity: g(x) changes exactly the links
+    # U_mu(x) and U_mu(x - mu) of those sites, so a half-sweep leaves the products
+    # U_mu(x-mu) U_mu(x) ... of the other parity's "stars" gauge-covariant.  Direct
+    # check: with every even site frozen to R = 1, the odd sites' update g(x) is
+    # recovered from U_0(x) alone and reproduces every other changed link.
+    U = fields.random_gauge_config(L4, 0.5, 14)
+    W = U.copy()
+    orc.or_half_sweep(W, 1, 1.7)
+    g = W[..., 0, :, :] @ obs.dag(U[..., 0, :, :])       # candidate g(x) from U_0(x)
+    t, z, y, x = np.indices(L4[::-1])
+    odd = ((t + z + y + x) % 2) == 1
+    one = np.eye(3)
+    gfull = np.where(odd[..., None, None], g, one)
+    V = U.copy()
+    for mu in range(4):
+        V[..., mu, :, :] = gfull @ U[..., mu, :, :] @ obs.dag(obs.shift(gfull, mu))
+    assert np.abs(V - W).max() < 1e-13
+
+
+def check_subgroup_fixed_point_after_site_update(orc, gauge):
+    # At omega = 1 the last subgroup step (1,2) maximises Re Tr[R K] on the K already
+    # rotated by the (0,1) and (0,2) steps, so the K rebuilt from the updated links
+    # (in-place Eq. 5) is a fixed point of that maximiser: R = 1.
+    nd = 4 if gauge == orc.LANDAU else 3
+    U = fields.random_gauge_config(L4, 0.5, 17)
+    orc.or_half_sweep(U, 0, 1.0, gauge)
+    for site in [(0, 0, 0, 0), (1, 2, 3, 0), (3, 3, 2, 2), (2, 1, 0, 3)]:
+        K = np.zeros((3, 3), complex)
+        for mu in range(nd):
+            b = list(site)
+            ax = obs.AXIS[mu]
+            b[ax] = (b[ax] - 1) % L4[0]
+            K += U[site][mu] + U[tuple(b)][mu].conj().T
+        a, bb = orc.su2_maximiser(K, 1, 2, 1.0)
+        assert abs(a - 1) < 1e-12 and abs(bb) < 1e-12, (site, a, bb)
+
+
+def check_even_translation_covariance_is_exact(orc):
+    U = fields.random_gauge_config((4, 4, 4, 6), 0.5, 15)
+    W = np.roll(U, shift=(2, 1, 1), axis=(0, 1, 3)).copy()   # shift by t+2, z+1, x+1: even
+    for k in range(3):
+        orc.sweep(U, 1.7)
+        orc.sweep(W, 1.7)
+    assert np.array_equal(np.roll(U, shift=(2, 1, 1), axis=(0, 1, 3)), W)
+
+
+def check_reunit_is_gram_schmidt_projection(orc):
+    rng = np.random.default_rng(8)
+    g = haar(50, 3)
+    noisy = g + 1e-3 * (rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape))
+    out = orc.reunit(noisy.copy())
+    assert obs.unitarity_error(out) < 1e-15 * 10 and obs.det_error(out) < 1e-14
+    for k in range(50):
+        q, r = np.linalg.qr(noisy[k].T)                    # columns of U^T = rows of U
+        q = q * (np.diag(r) / np.abs(np.diag(r)))            # positive diagonal of R
+        assert np.abs(out[k][:2] - q.T[:2]).max() < 1e-14
+    exact = orc.reunit(g.copy())
+    assert np.abs(exact - g).max() < 1e-14
+
+
+# --- Algorithm 1: the driver, and end-to-end closed forms ------------------------------
+
+def check_fix_stop_rule_and_bookkeeping(orc):
+    U = fields.random_gauge_config(L4, 0.4, 16)
+    W = U.copy()
+    eps = 1e-10
+    r = orc.fix(U, eps, 200, 1.7, reunit_interval=20)
+    assert r["rc"] == 0 and r["theta"] < eps
+    n = r["iters"]
+    assert r["theta_hist"][n - 1] >= eps and r["theta_hist"][n] == r["theta"]
+    # the same sweeps by hand give the same bits
+    for k in range(n):
+        orc.sweep(W, 1.7, reunit=((k + 1) % 20 == 0))
+    assert np.array_equal(U, W)
+    rmax = orc.fix(fields.random_gauge_config(L4, 0.4, 16), 1e-30, 7, 1.7)
+    assert rmax["rc"] == 1 and rmax["iters"] == 7
+
+
+def check_pure_gauge_reaches_unit_field(orc, seed):
+    # U = h(x) h(x+mu)^+ is a gauge transform of U = 1, whose maximum is F = 1,
+    # theta = 0, every link = 1 (Re Tr U = 3 only for U = 1).  For these fixed seeds
+    # overrelaxation reaches it (other seeds may stop at a lattice Gribov copy).
+    U = fields.pure_gauge_config(L4, seed)
+    r = orc.fix(U, 1e-15, 2000, 1.7)
+    assert r["rc"] == 0
+    assert abs(r["F"] - 1) < 1e-12
+    assert np.abs(U - np.eye(3)).max() < 1e-6
+
+
+def check_smooth_field_recovered_functional(orc):
+    # The field before the random gauge transformation is a near-identity field; the
+    # fixed field should reach a functional at least as large (not guaranteed in
+    # general because of Gribov copies; fixed seed).
+    dims = (6, 6, 6, 6)
+    U0 = fields.smooth_field(dims, 0.4, 1)
+    U = fields.random_gauge_config(dims, 0.4, 1, 2)
+    r = orc.fix(U, 1e-12, 1000, 1.7)
+    assert r["rc"] == 0
+    assert r["F"] >= orc.measure(U0)[0]
+
+
+def check_coulomb_slices_fix_independently(orc):
+    # Coulomb gauge (mu < 3 in K, F, Delta; Section 1 below Eq. 3) decouples the time
+    # slices: each slice of a 4D run equals that slice fixed on its own.  A lone slice t
+    # is placed in a (Lx, Ly, Lz, 2) lattice at time t mod 2 so its site parities agree.
+    dims = (4, 4, 6, 4)
+    U = fields.random_gauge_config(dims, 0.5, 30)
+    U4 = U.copy()
+    eps = 1e-12
+    r = orc.fix(U4, eps, 3000, 1.7, gauge=orc.COULOMB)
+    assert r["rc"] == 0
+    for t in range(dims[3]):
+        S = np.broadcast_to(np.eye(3, dtype=complex), (2,) + U.shape[1:]).copy()
+        S[t % 2] = U[t]
+        other = np.ones(2, np.uint8)
+        other[1 - t % 2] = 0
+        # run the lone slice with the other slice masked out, same stop rule
+        it = 0
+        F, th, F_t, th_t = orc.measure(S, orc.COULOMB)
+        while th_t[t % 2] >= eps and it < 3000:
+            orc.or_half_sweep(S, 0, 1.7, orc.COULOMB, slice_active=other)
+            orc.or_half_sweep(S, 1, 1.7, orc.COULOMB, reunit_after=((it + 1) % 20 == 0),
+                                 slice_active=other)
+            it += 1
+            F, th, F_t, th_t = orc.measure(S, orc.COULOMB)
+        assert it == r["slice_iters"][t]
+        assert np.abs(S[t % 2][..., :3, :, :] - U4[t][..., :3, :, :]).max() < 1e-12
+
+
+def check_coulomb_per_slice_masks_freeze_converged_slices(orc):
+    dims = (4, 4, 4, 6)
+    U = fields.random_gauge_config(dims, 0.5, 31)
+    r = orc.fix(U, 1e-12, 500, 1.7, gauge=orc.COULOMB)
+    F, th, F_t, th_t = orc.measure(U, orc.COULOMB)
+    assert np.all(th_t < 1e-12)
+    assert len(set(r["slice_iters"].tolist())) > 1      # slices stop at different sweeps
+    assert r["iters"] == r["slice_iters"].max()
