@@ -1,0 +1,350 @@
+"""Benchmark: 32^4 SU(3) Landau gauge fixing by checkerboard overrelaxation on GB300.
+
+One step = one pass of the whole hot path over the lattice: the even and the odd
+half-sweep of Algorithm 1 (K(x), the three SU(2)-subgroup maximisers with omega = 1.7,
+g(x) applied to the 8 links; links reunitarised after every 20th sweep inside the odd
+half-sweep) followed by the F / theta reduction of Eqs. (1)-(3) (odd-site theta fused
+into the odd half-sweep, one even-site pass, one finishing reduction), on FP32 links
+stored as 12 reals.  Metric: effective link bandwidth, algorithmic link bytes of a step
+(16 V b for the sweep + 4 V b for the theta pass, b = 48 B) over the step time.
+
+Also reported: the roofline of the half-sweep kernel (bytes 8 V b per launch over its
+CUDA-event duration, against the measured HBM copy bandwidth), the same metric end to
+end through the C ABI with host buffers, time to theta < 1e-15 for mixed FP32->FP64
+versus pure FP64 fixing, and the CPU oracle timed on the host cores.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "32^4 SU(3) OR sweep link GB/s vs HBM peak; time to θ<1e-15, mixed vs FP64"
+DIMS = (32, 32, 32, 32)
+EPS_FIELD, SEED = 0.5, 3
+OMEGA = 1.7
+LINK_B = 48                    # FP32, 12 reals
+V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
+STEP_BYTES = 20 * V * LINK_B   # sweep 16 V b + theta pass 4 V b
+HALF_SWEEP_BYTES = 8 * V * LINK_B
+WORKLOAD = "landau-32^4-fp32-12: OR sweep (even+odd, omega 1.7, reunit every 20) + F/theta"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.proc, self.lines = index, None, []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_field(dims=DIMS, eps=EPS_FIELD, seed=SEED):
+    from paper_1412_1498_gb300 import fields
+    return fields.random_gauge_config(dims, eps, seed)
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_steps(U, budget_s: float | None = None, max_steps: int | None = None, first: int = 0):
+    """Oracle steps (sweep + F/theta) on U until budget_s seconds or max_steps; (steps, s)."""
+    import oracle
+    n, t0 = 0, time.perf_counter()
+    while True:
+        oracle.sweep(U, OMEGA, oracle.LANDAU, reunit=((first + n + 1) % 20 == 0))
+        oracle.measure(U, oracle.LANDAU)
+        n += 1
+        el = time.perf_counter() - t0
+        if (budget_s is not None and el >= budget_s) or (max_steps is not None and n >= max_steps):
+            return n, el
+
+
+def run_reference(args):
+    """The oracle on the host cores, same workload / metric / unit (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    threads = oracle.num_threads()
+    # One step = one sweep + F/theta.  The sample is the full 32^4 lattice unless K + W
+    # steps of it would take more than about two minutes; then a 32^3 x Lt slab (Lt even)
+    # of the same field recipe, and the metric counts that slab's bytes.
+    dims = DIMS
+    probe = make_field((32, 32, 32, 4))
+    _, t4 = oracle_steps(probe, max_steps=1)
+    per_slice = t4 / 4
+    total = args.steps + args.warmup
+    if total * per_slice * 32 > 120.0:
+        lt = max(2, int(120.0 / (total * per_slice)) // 2 * 2)
+        dims = (32, 32, 32, min(32, lt))
+    U = make_field(dims)
+    if args.warmup:
+        oracle_steps(U, max_steps=args.warmup)
+    t0 = time.perf_counter()
+    oracle_steps(U, max_steps=args.steps, first=args.warmup)
+    el = time.perf_counter() - t0
+    vol = dims[0] * dims[1] * dims[2] * dims[3]
+    value = 20 * vol * LINK_B * args.steps / el / 1e9
+    sample = (f"{args.steps} steps on a {'x'.join(map(str, dims))} lattice of the 32^4 workload's "
+              "field recipe (FP64 oracle, 18 reals per link, OpenMP over one parity)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "lattice": list(DIMS)},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ------------------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1412_1498_gb300 import gf
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    U = make_field()        # each rank: its own independent 32^4 lattice (weak scaling)
+    stream = torch.cuda.current_stream(dev)
+    fx = gf.GaugeFixer(DIMS, gf.GF_LANDAU, gf.GF_FP32_12, device=dev)
+    gf.gf_set_check_interval(fx.h, 1)
+    gf.gf_set_reunit_interval(fx.h, 20)
+    fx.upload(U)
+
+    # ---- block size: pick the fastest half-sweep launch shape (64 / 128 / 256 threads)
+    best = None
+    for threads in (64, 128, 256):
+        gf.gf_set_block_size(fx.h, threads)
+        for _ in range(3):
+            fx.or_sweep(2, OMEGA)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            fx.or_sweep(2, OMEGA)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 20
+        if best is None or ms < best[1]:
+            best = (threads, ms)
+    gf.gf_set_block_size(fx.h, best[0])
+    fx.upload(U)
+
+    # ---- warm-up steps (untimed)
+    if args.warmup:
+        gf.gf_fix(fx.h, 1e-300, args.warmup)
+    fx.upload(U)
+    barrier()
+
+    # ---- timed region: K steps through gf_fix (device-driven loop, CUDA graphs)
+    with ClockSampler(local) as clocks:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        rc, iters, F, th = gf.gf_fix(fx.h, 1e-300, args.steps)
+        e1.record(stream)
+        barrier()
+        ms_total = e0.elapsed_time(e1)
+        # roofline: the half-sweep kernel alone, back to back on the same stream
+        n_half = 2 * max(20, args.steps // 2)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        for _ in range(n_half // 2):
+            fx.or_sweep(2, OMEGA)
+        k1.record(stream)
+        k1.synchronize()
+        half_ms = k0.elapsed_time(k1) / n_half
+    assert int(iters[0]) == args.steps, (iters, args.steps)
+    ms_total = max_over_ranks(ms_total)
+    ms_step = ms_total / args.steps
+    value = world * STEP_BYTES * args.steps / (ms_total * 1e-3) / 1e9
+    graph_sweeps = 16
+    launches = 3 + ((args.steps + graph_sweeps - 1) // graph_sweeps) * graph_sweeps * 4
+
+    # ---- end to end through the C ABI with pinned host buffers: upload, one step, download
+    Uh = torch.from_numpy(U).pin_memory()
+    out = torch.empty_like(Uh).pin_memory()
+    e2e_steps = max(3, min(10, args.steps))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        fx.upload(Uh)
+        gf.gf_fix(fx.h, 1e-300, 1)
+        fx.download(out=out)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0) / e2e_steps
+    e2e_value = world * STEP_BYTES / e2e_s / 1e9
+    canon_bytes = 4 * V * 144
+
+    # ---- time to theta < 1e-15: mixed FP32-12 -> FP64-18 vs pure FP64-18
+    ttt = None
+    if not args.skip_time_to_theta:
+        ttt = {}
+        for name, storage, mixed in (("mixed", gf.GF_FP32_12, True), ("fp64", gf.GF_FP64_18, False)):
+            f2 = gf.GaugeFixer(DIMS, gf.GF_LANDAU, storage, mixed=mixed, device=dev)
+            f2.upload(U)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = f2.fix(1e-15, args.max_sweeps)
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            ttt[name] = dict(seconds=el, sweeps=int(r["iters"][0]), phase_sweeps=list(r["phase_sweeps"]),
+                             converged=r["rc"] == gf.GF_OK, F=float(r["F"][0]), theta=float(r["theta"][0]))
+            f2.close()
+            del f2
+            torch.cuda.empty_cache()
+        ttt["F_err_mixed_vs_fp64"] = abs(ttt["mixed"]["F"] - ttt["fp64"]["F"])
+        ttt["theta_mixed"] = ttt["mixed"]["theta"]
+        ttt["speedup_mixed_over_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]
+
+    peak, peak_kind = measured_peaks()
+    achieved = HALF_SWEEP_BYTES / (half_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "k_or_sweep<FP32_12, Landau>",
+                "bytes_per_launch": HALF_SWEEP_BYTES, "ms_per_launch": half_ms,
+                "peak_kind": f"{peak_kind} HBM copy bandwidth"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import oracle
+        oracle.build()
+        Uc = U.copy()
+        n, el = oracle_steps(Uc, budget_s=args.cpu_seconds)
+        cpu = {"value": STEP_BYTES * n / el / 1e9, "unit": "GB/s", "cores": oracle.num_threads(),
+               "kind": "oracle", "sample": f"{n} steps of the full 32^4 workload in {el:.1f} s "
+                                            "(FP64 oracle, 18 reals per link, OpenMP over one parity)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "storage": "fp32-12", "omega": OMEGA,
+                       "check_interval": 1, "reunit_interval": 20, "block_threads": best[0],
+                       "field": f"smooth eps={EPS_FIELD} seed={SEED} + Haar gauge",
+                       "l2": "inputs larger than L2: 201 MB of links vs 129 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": canon_bytes,
+                    "d2h_bytes_per_step": canon_bytes},
+            "gpu_launches": launches,
+            "clocks": clocks.summary(),
+            "time_to_theta_1e-15": ttt,
+        }
+        print(json.dumps(line))
+    fx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gf", choices=["gf", "reference"])
+    ap.add_argument("--max-sweeps", type=int, default=20000)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--skip-time-to-theta", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gf":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

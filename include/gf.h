@@ -1,0 +1,194 @@
+/*
+ * gf.h -- C ABI of libgf: SU(3) Landau / Coulomb gauge fixing by checkerboard
+ * overrelaxation on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: N. Cardoso, "Coulomb and Landau Gauge Fixing in GPUs using CUDA and MILC"
+ * (Lattice 2014).  The gauge condition is the maximum of the functional F_U[g] of
+ * Eq. (1); its quality is theta of Eqs. (2)-(3); the overrelaxation algorithm is
+ * Algorithm 1 with the local SU(2)-subgroup maximisation of Eqs. (4)-(6).
+ *
+ * Conventions used by every call
+ * -------------------------------
+ *  - dims = {Lx, Ly, Lz, Lt}; every extent even and >= 2 (Section 2 requires even local
+ *    extents for the checkerboard); direction mu = 0, 1, 2, 3 is x, y, z, t (time is
+ *    mu = 3, Section 1).  Periodic boundaries in every direction.
+ *  - Canonical field layout (host or device buffers passed to upload/download):
+ *    interleaved (re, im) float64 pairs of a complex array of shape
+ *    (Lt, Lz, Ly, Lx, 4, 3, 3), row-major, x fastest: link U_mu(x) of site
+ *    s = x + Lx*(y + Ly*(z + Lz*t)) starts at element 2*9*(4*s + mu).
+ *  - Site parity p(x) = (x + y + z + t) mod 2; parity 0 ("even") is updated first.
+ *  - Landau gauge uses nd = 4 directions in K(x), F and Delta(x); Coulomb gauge uses
+ *    nd = 3 (the temporal links are still transformed, Algorithm 1 "for all mu").
+ *    F is normalised by 1/(nd * 3 * V) so that the unit field has F = 1.
+ *  - A handle holds one lattice (gf_create) or a batch of independent lattices
+ *    (gf_create_batch).  Convergence units: one per lattice for Landau gauge, one per
+ *    (lattice, time slice) for Coulomb gauge; each unit has its own stop rule and mask.
+ *  - Streams: every call enqueues work on the CUDA stream given at creation (NULL =
+ *    legacy default stream).  Calls that return host values synchronise that stream.
+ *  - Memory: the caller may pass a device workspace of at least gf_workspace_bytes()
+ *    bytes (e.g. a framework's caching allocator); the handle then allocates no device
+ *    memory of its own.  With workspace == NULL the handle allocates it with cudaMalloc
+ *    and frees it in gf_destroy.  The caller keeps ownership of every buffer it passes.
+ *  - Errors: every int-returning call returns GF_OK (0) on success, a negative GF_E*
+ *    code on failure (nothing is left half-done on the host; device work already
+ *    enqueued may have run), or GF_ENOTCONVERGED (positive, not a failure).  No C++
+ *    exception crosses this interface.  gf_last_error() gives a readable message.
+ *  - Handles are not thread-safe: one host thread at a time per handle.
+ */
+#ifndef GF_H
+#define GF_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define GF_API __attribute__((visibility("default")))
+#else
+#define GF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define GF_OK 0
+#define GF_ENOTCONVERGED 1 /* gf_fix stopped at maxiter with a unit still above eps */
+#define GF_EINVAL (-1)     /* bad argument: dims, enum, null pointer, size */
+#define GF_ECUDA (-2)      /* a CUDA runtime call failed; see gf_last_error */
+#define GF_ENOMEM (-3)     /* workspace too small or device allocation failed */
+#define GF_ESTATE (-4)     /* call not valid in the handle's current state */
+
+/* gauge condition (Section 1, Eq. (3) and the sentence after it) */
+#define GF_LANDAU 0
+#define GF_COULOMB 1
+
+/* link storage in device memory (Section 2: 18 or 12 real numbers per SU(3) link) */
+#define GF_FP64_18 0 /* full matrix, FP64 */
+#define GF_FP32_18 1 /* full matrix, FP32 */
+#define GF_FP32_12 2 /* rows 0 and 1, FP32; row 2 = conj(row0 x row1) on every load */
+
+/* creation flags */
+#define GF_FLAG_MIXED 1 /* keep an FP64-18 copy: gf_fix runs the FP32 storage down to the
+                           switch threshold, converts, then polishes in FP64 */
+
+/* form of the overrelaxation g -> g^omega per SU(2) subgroup (Section 1, after Eq. (6)) */
+#define GF_OR_FIRST_ORDER 0 /* a' = 1 - omega + omega a, b' = omega b, renormalised */
+#define GF_OR_EXACT 1       /* exact SU(2) power of the subgroup maximiser */
+
+typedef struct gf_handle gf_handle;
+
+/*
+ * Bytes of device workspace a handle needs.
+ *   n_lat: number of lattices (1 for gf_create); dims: n_lat * 4 ints as above;
+ *   gauge: GF_LANDAU | GF_COULOMB; storage: GF_FP64_18 | GF_FP32_18 | GF_FP32_12;
+ *   flags: 0 or GF_FLAG_MIXED.  *bytes receives the size.  Returns GF_EINVAL on bad
+ *   arguments.
+ */
+GF_API int gf_workspace_bytes(int n_lat, const int *dims, int gauge, int storage, int flags,
+                       size_t *bytes);
+
+/*
+ * Create a handle for one lattice (Section 1 problem statement; Eq. (1) with Nc = 3).
+ *   dims: {Lx, Ly, Lz, Lt}, even, >= 2.  nc: must be 3 (GF_EINVAL otherwise).
+ *   stream: a cudaStream_t (or NULL).  workspace / workspace_bytes: caller-owned device
+ *   memory (16-byte aligned, >= gf_workspace_bytes) or NULL / 0.
+ *   *out receives the handle; on failure *out is NULL.  The links start undefined:
+ *   call gf_upload before sweeping.
+ */
+GF_API int gf_create(const int dims[4], int nc, int gauge, int storage, int flags, void *stream,
+              void *workspace, size_t workspace_bytes, gf_handle **out);
+
+/*
+ * Create a handle for n_lat independent lattices of possibly different extents (a batch
+ * of configurations fixed together: one launch per half-sweep covers all of them).
+ *   dims: n_lat * 4 ints.  Other arguments as gf_create.
+ */
+GF_API int gf_create_batch(int n_lat, const int *dims, int gauge, int storage, int flags,
+                    void *stream, void *workspace, size_t workspace_bytes, gf_handle **out);
+
+/* Release the handle (and the workspace, if the handle allocated it).  NULL is a no-op. */
+GF_API void gf_destroy(gf_handle *h);
+
+/* Message of the last failure on this handle ("" if none); h == NULL gives the message of
+   the last failed gf_create / gf_create_batch on this thread.  Valid until the next call. */
+GF_API const char *gf_last_error(const gf_handle *h);
+
+/* Number of lattices and of convergence units (see conventions). */
+GF_API int gf_num_lattices(const gf_handle *h);
+GF_API int gf_num_units(const gf_handle *h);
+
+/*
+ * Copy lattice `lat` of the batch in (upload) or out (download), converting between the
+ * canonical layout and the internal structure-of-arrays layout (Section 2: parity-split
+ * sites, each complex element of a link at a stride of 4 V).
+ *   links: canonical layout, 2*9*4*V float64; on_device = 1 if it is device memory,
+ *   0 if host memory (pinned memory gives the fastest copies).
+ *   Upload rounds to the handle's storage (FP32 and/or 12 reals: row 2 is dropped) and
+ *   resets the sweep counter, the masks (all units active) and the iteration counts.
+ *   Download reconstructs row 2 in FP64 for 12-real storage.  In mixed mode gf_fix
+ *   leaves the field in the FP64 copy and download reads that copy; an upload moves
+ *   the handle back to its primary storage, so upload every lattice of a batch before
+ *   the next gf_fix.  Device buffers must be 16-byte aligned.  Both calls synchronise
+ *   the stream when on_device = 0 (the host buffer is complete on return).
+ */
+GF_API int gf_upload(gf_handle *h, int lat, const double *links, int on_device);
+GF_API int gf_download(gf_handle *h, int lat, double *links, int on_device);
+
+/*
+ * F (Eq. (1), in-place links so g = 1) and theta (Eqs. (2)-(3)) of the current field.
+ *   F, theta: n_lat entries each (nullable).  unit_F, unit_theta: gf_num_units entries
+ *   each (nullable); for Coulomb gauge unit (lat, t) has F_t and theta_t normalised by
+ *   the slice volume.  Sums are accumulated in FP64 in a fixed order (bit-reproducible
+ *   for a given handle).  Synchronises the stream.
+ */
+GF_API int gf_functional_theta(gf_handle *h, double *F, double *theta, double *unit_F,
+                        double *unit_theta);
+
+/*
+ * One checkerboard half-sweep (parity 0 or 1) or a full sweep (parity 2 = even then
+ * odd) of Algorithm 1 over all active units, with overrelaxation parameter omega in
+ * [1, 2) (Section 1, after Eq. (6)).  Per site: K(x) of Eq. (5) in place, the three
+ * SU(2)-subgroup maximisers (0,1), (0,2), (1,2) with g -> g^omega, and g(x) applied
+ * to U_mu(x) and U_mu(x - mu) for all four mu.  Asynchronous; no reunitarisation.
+ */
+GF_API int gf_or_sweep(gf_handle *h, int parity, double omega);
+
+/* Project every link of the current field back to SU(3) (Gram-Schmidt on rows 0, 1;
+   row 2 = conj(row0 x row1)), as done every 20 sweeps in Section 3.  Asynchronous. */
+GF_API int gf_reunitarize(gf_handle *h);
+
+/*
+ * Algorithm 1: measure; while a unit has theta >= eps and fewer than maxiter sweeps
+ * were done: even half-sweep, odd half-sweep (reunitarising the links it writes after
+ * every reunit_interval-th sweep), then F and theta every check_interval sweeps; a
+ * unit whose theta < eps is masked and no longer updated.  The sweep counter for the
+ * reunitarisation schedule starts at 0 in each call.
+ *   eps > 0; maxiter >= 0.  iters (nullable): gf_num_units ints, sweeps each unit
+ *   received.  F, theta (nullable): n_lat final values.
+ *   With GF_FLAG_MIXED: FP32 sweeps until every unit has theta < the switch threshold
+ *   (gf_set_mixed_switch, default 1e-8) or maxiter, then conversion to FP64-18 with a
+ *   reunitarisation, then FP64 sweeps until theta < eps; iters counts both phases.
+ *   Returns GF_OK when every unit converged, GF_ENOTCONVERGED at maxiter.
+ *   Synchronises the stream.
+ */
+GF_API int gf_fix(gf_handle *h, double eps, int maxiter, int *iters, double *F, double *theta);
+
+/* Settings (defaults in brackets).  Each returns GF_EINVAL for an out-of-range value. */
+GF_API int gf_set_omega(gf_handle *h, double omega);          /* [1.7], 1 <= omega < 2       */
+GF_API int gf_set_overrelax_form(gf_handle *h, int form);     /* [GF_OR_FIRST_ORDER]          */
+GF_API int gf_set_reunit_interval(gf_handle *h, int n);       /* [20], 0 = never              */
+GF_API int gf_set_check_interval(gf_handle *h, int n);        /* [1], >= 1                    */
+GF_API int gf_set_mixed_switch(gf_handle *h, double eps_sw);  /* [1e-8], > 0                  */
+GF_API int gf_set_reproducible(gf_handle *h, int on);         /* [0]; 1 = FP64 kernels without
+                                  fused multiply-add and with IEEE divisions, in the
+                                  oracle's operation order (bit-reproducible results) */
+GF_API int gf_set_block_size(gf_handle *h, int threads);      /* [autotuned]; 64, 128 or 256  */
+
+/* Sweeps done by the last gf_fix in the FP32 and FP64 phases (mixed mode), nullable. */
+GF_API int gf_fix_phase_sweeps(const gf_handle *h, int *fp32_sweeps, int *fp64_sweeps);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GF_H */

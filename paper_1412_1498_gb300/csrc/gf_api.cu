@@ -1,0 +1,690 @@
+// gf_api.cu -- host implementation of the C ABI declared in include/gf.h.
+//
+// Algorithm 1 of the paper as a device-driven loop: each sweep is four launches
+// (even half-sweep, odd half-sweep with fused reunitarisation and odd-site theta,
+// even-site F/theta pass, finishing reduction) that read and update a small DevState
+// in device memory, so that a captured CUDA graph of many sweeps needs no host
+// decision between them.  The host synchronises once per graph replay to read the
+// number of still-active convergence units.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gf.h"
+#include "gf_kernels.cuh"
+
+namespace gf {
+void launch_sweep_fp64(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_sweep_fp64_repro(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_measure_fp64(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_measure_fp32(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
+                         cudaStream_t s);
+void launch_fill_int(int* p, int value, int n, cudaStream_t s);
+
+void launch_sweep(int storage, int nd, bool repro, const SweepArgs& a, int n_tiles, int threads,
+                  cudaStream_t s) {
+  if (storage == GF_FP64_18) {
+    if (repro) launch_sweep_fp64_repro(nd, a, n_tiles, threads, s);
+    else launch_sweep_fp64(nd, a, n_tiles, threads, s);
+  } else {
+    launch_sweep_fp32(storage, nd, a, n_tiles, threads, s);
+  }
+}
+
+void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
+                    cudaStream_t s) {
+  if (storage == GF_FP64_18) launch_measure_fp64(nd, a, n_tiles, threads, s);
+  else launch_measure_fp32(storage, nd, a, n_tiles, threads, s);
+}
+}  // namespace gf
+
+using namespace gf;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kStagingMax = 32u << 20;  // bytes of canonical links per host copy
+constexpr int kMinThreads = 64;
+constexpr int kGraphSweeps = 16;
+thread_local std::string g_create_error;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int link_bytes(int storage) {
+  return storage == GF_FP64_18 ? 144 : storage == GF_FP32_18 ? 72 : 48;
+}
+
+struct Layout {
+  size_t links, links64, staging, lats, lats64, tiles, unit_tiles, unit_lat, active, iters, partF,
+      pthe, ptho, usF, usT, uF, uT, lF, lT, state, total;
+  size_t staging_bytes;
+  int max_tiles, n_units;
+};
+
+bool valid_dims(const int* d) {
+  for (int k = 0; k < 4; ++k)
+    if (d[k] < 2 || (d[k] % 2) != 0) return false;
+  long long V = (long long)d[0] * d[1] * d[2] * d[3];
+  return V / 2 < (1LL << 30);  // half-volumes and plane indices stay in 32 bits
+}
+
+int tiles_for(const int* d, int threads) {
+  const long long V3h = (long long)d[0] * d[1] * d[2] / 2;
+  return (int)(d[3] * ((V3h + threads - 1) / threads));
+}
+
+// Carve the workspace: every region 256-byte aligned.
+bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout* L) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  long long sites = 0, vmax = 0;
+  int max_tiles = 0, n_units = 0;
+  for (int l = 0; l < n_lat; ++l) {
+    const int* d = dims + 4 * l;
+    long long V = (long long)d[0] * d[1] * d[2] * d[3];
+    sites += V;
+    vmax = std::max(vmax, V);
+    max_tiles += tiles_for(d, kMinThreads);
+    n_units += gauge == GF_LANDAU ? 1 : d[3];
+  }
+  L->links = take((size_t)sites * 4 * link_bytes(storage));
+  const bool mixed = (flags & GF_FLAG_MIXED) && storage != GF_FP64_18;
+  L->links64 = mixed ? take((size_t)sites * 4 * 144) : (size_t)-1;
+  size_t canon = (size_t)vmax * 4 * 144;
+  size_t site_bytes = 4 * 144;
+  L->staging_bytes = std::max(site_bytes, std::min(canon, kStagingMax) / site_bytes * site_bytes);
+  L->staging = take(L->staging_bytes);
+  L->lats = take(sizeof(LatDev) * n_lat);
+  L->lats64 = take(sizeof(LatDev) * n_lat);
+  L->tiles = take(sizeof(int4) * max_tiles);
+  L->unit_tiles = take(sizeof(int) * (n_units + 1));
+  L->unit_lat = take(sizeof(int) * n_units);
+  L->active = take(sizeof(int) * n_units);
+  L->iters = take(sizeof(int) * n_units);
+  L->partF = take(sizeof(double) * max_tiles);
+  L->pthe = take(sizeof(double) * max_tiles);
+  L->ptho = take(sizeof(double) * max_tiles);
+  L->usF = take(sizeof(double) * n_units);
+  L->usT = take(sizeof(double) * n_units);
+  L->uF = take(sizeof(double) * n_units);
+  L->uT = take(sizeof(double) * n_units);
+  L->lF = take(sizeof(double) * n_lat);
+  L->lT = take(sizeof(double) * n_lat);
+  L->state = take(sizeof(DevState));
+  L->total = off;
+  L->max_tiles = max_tiles;
+  L->n_units = n_units;
+  return true;
+}
+
+int check_common(int n_lat, const int* dims, int gauge, int storage, int flags, std::string* why) {
+  if (n_lat < 1 || !dims) { *why = "need at least one lattice"; return GF_EINVAL; }
+  if (gauge != GF_LANDAU && gauge != GF_COULOMB) { *why = "gauge must be GF_LANDAU or GF_COULOMB"; return GF_EINVAL; }
+  if (storage != GF_FP64_18 && storage != GF_FP32_18 && storage != GF_FP32_12) {
+    *why = "storage must be GF_FP64_18, GF_FP32_18 or GF_FP32_12";
+    return GF_EINVAL;
+  }
+  if (flags & ~GF_FLAG_MIXED) { *why = "unknown flag"; return GF_EINVAL; }
+  for (int l = 0; l < n_lat; ++l)
+    if (!valid_dims(dims + 4 * l)) {
+      char buf[160];
+      snprintf(buf, sizeof buf, "lattice %d: every extent must be even and >= 2 (got %d %d %d %d)", l,
+               dims[4 * l], dims[4 * l + 1], dims[4 * l + 2], dims[4 * l + 3]);
+      *why = buf;
+      return GF_EINVAL;
+    }
+  return GF_OK;
+}
+
+}  // namespace
+
+struct gf_handle {
+  int n_lat = 0, gauge = 0, nd = 4, storage = 0, flags = 0;
+  std::vector<int> dims;
+  cudaStream_t stream = nullptr, cap_stream = nullptr;
+  bool own_ws = false;
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  Layout L{};
+  // device regions
+  char *links = nullptr, *links64 = nullptr, *staging = nullptr;
+  LatDev *d_lats = nullptr, *d_lats64 = nullptr;
+  int4* d_tiles = nullptr;
+  int *d_unit_tiles = nullptr, *d_unit_lat = nullptr, *d_active = nullptr, *d_iters = nullptr;
+  double *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr;
+  double *d_usF = nullptr, *d_usT = nullptr, *d_uF = nullptr, *d_uT = nullptr, *d_lF = nullptr,
+         *d_lT = nullptr;
+  DevState* d_state = nullptr;
+  // host copies
+  std::vector<LatDev> lats, lats64;
+  int n_tiles = 0, n_units = 0, threads = 128;
+  // settings
+  double omega = 1.7, eps_switch = 1e-8;
+  int form = GF_OR_FIRST_ORDER, reunit_interval = 20, check_interval = 1;
+  bool repro = false;
+  // state
+  int cur = 0;  // 0: primary buffer holds the field, 1: FP64 polish buffer
+  int phase_sweeps[2] = {0, 0};
+  // graphs: one per buffer
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  std::string err;
+};
+
+namespace {
+
+int fail(gf_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define GF_CK(h, call)                                                                     \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      return fail(h, GF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));        \
+  } while (0)
+
+#define GF_CK_LAUNCH(h) GF_CK(h, cudaGetLastError())
+
+void drop_graphs(gf_handle* h) {
+  for (auto& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int cur_storage(const gf_handle* h) { return h->cur == 1 ? GF_FP64_18 : h->storage; }
+char* cur_links(const gf_handle* h) { return h->cur == 1 ? h->links64 : h->links; }
+LatDev* cur_lats(const gf_handle* h) { return h->cur == 1 ? h->d_lats64 : h->d_lats; }
+const LatDev& cur_lat_host(const gf_handle* h, int l) { return h->cur == 1 ? h->lats64[l] : h->lats[l]; }
+
+// Build the tile table for the current block size and upload it.
+int build_tiles(gf_handle* h) {
+  std::vector<int4> tiles;
+  std::vector<int> unit_tiles, unit_lat;
+  for (int l = 0; l < h->n_lat; ++l) {
+    const LatDev& lat = h->lats[l];
+    if (h->gauge == GF_LANDAU) {
+      unit_tiles.push_back((int)tiles.size());
+      unit_lat.push_back(l);
+    }
+    for (int t = 0; t < lat.L[3]; ++t) {
+      if (h->gauge == GF_COULOMB) {
+        unit_tiles.push_back((int)tiles.size());
+        unit_lat.push_back(l);
+      }
+      const int unit = lat.unit0 + (h->gauge == GF_COULOMB ? t : 0);
+      for (int h3 = 0; h3 < lat.V3h; h3 += h->threads) tiles.push_back(make_int4(l, t, h3, unit));
+    }
+  }
+  unit_tiles.push_back((int)tiles.size());
+  if ((int)tiles.size() > h->L.max_tiles) return fail(h, GF_EINVAL, "tile table overflow");
+  h->n_tiles = (int)tiles.size();
+  GF_CK(h, cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
+  GF_CK(h, cudaMemcpyAsync(h->d_unit_tiles, unit_tiles.data(), sizeof(int) * unit_tiles.size(),
+                           cudaMemcpyHostToDevice, h->stream));
+  GF_CK(h, cudaMemcpyAsync(h->d_unit_lat, unit_lat.data(), sizeof(int) * unit_lat.size(),
+                           cudaMemcpyHostToDevice, h->stream));
+  GF_CK(h, cudaStreamSynchronize(h->stream));  // host vectors die on return
+  drop_graphs(h);
+  return GF_OK;
+}
+
+SweepArgs sweep_args(gf_handle* h, int parity, bool loop) {
+  SweepArgs a{};
+  a.links = cur_links(h);
+  a.lats = cur_lats(h);
+  a.tiles = h->d_tiles;
+  a.active = loop ? h->d_active : nullptr;
+  a.st = loop ? h->d_state : nullptr;
+  a.part_theta = h->d_ptho;
+  a.parity = parity;
+  a.form = h->form;
+  a.reunit = 0;
+  a.measure = 0;
+  a.omega = h->omega;
+  return a;
+}
+
+MeasureArgs measure_args(gf_handle* h, int parity, bool loop) {
+  MeasureArgs a{};
+  a.links = cur_links(h);
+  a.lats = cur_lats(h);
+  a.tiles = h->d_tiles;
+  a.active = loop ? h->d_active : nullptr;
+  a.st = loop ? h->d_state : nullptr;
+  a.part_F = parity == 0 ? h->d_partF : nullptr;
+  a.part_theta = parity == 0 ? h->d_pthe : h->d_ptho;
+  a.parity = parity;
+  return a;
+}
+
+FinishArgs finish_args(gf_handle* h, int mode) {
+  FinishArgs a{};
+  a.lats = cur_lats(h);
+  a.unit_tiles = h->d_unit_tiles;
+  a.unit_lat = h->d_unit_lat;
+  a.active = h->d_active;
+  a.iters = h->d_iters;
+  a.part_F = h->d_partF;
+  a.part_th_even = h->d_pthe;
+  a.part_th_odd = h->d_ptho;
+  a.unit_sumF = h->d_usF;
+  a.unit_sumTh = h->d_usT;
+  a.unit_F = h->d_uF;
+  a.unit_theta = h->d_uT;
+  a.lat_F = h->d_lF;
+  a.lat_theta = h->d_lT;
+  a.st = h->d_state;
+  a.n_units = h->n_units;
+  a.n_lat = h->n_lat;
+  a.nd = h->nd;
+  a.mode = mode;
+  return a;
+}
+
+// F and theta of every unit and lattice, all units (mode MEASURE or RESET), async.
+int enqueue_measure_all(gf_handle* h, int mode) {
+  const int st = cur_storage(h);
+  launch_measure(st, h->nd, measure_args(h, 0, false), h->n_tiles, h->threads, h->stream);
+  GF_CK_LAUNCH(h);
+  launch_measure(st, h->nd, measure_args(h, 1, false), h->n_tiles, h->threads, h->stream);
+  GF_CK_LAUNCH(h);
+  launch_finish(finish_args(h, mode), h->stream);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+// One sweep of the device-driven loop (four launches).
+int enqueue_loop_sweep(gf_handle* h, cudaStream_t s) {
+  const int st = cur_storage(h);
+  launch_sweep(st, h->nd, h->repro, sweep_args(h, 0, true), h->n_tiles, h->threads, s);
+  GF_CK_LAUNCH(h);
+  launch_sweep(st, h->nd, h->repro, sweep_args(h, 1, true), h->n_tiles, h->threads, s);
+  GF_CK_LAUNCH(h);
+  launch_measure(st, h->nd, measure_args(h, 0, true), h->n_tiles, h->threads, s);
+  GF_CK_LAUNCH(h);
+  launch_finish(finish_args(h, FINISH_LOOP), s);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+int ensure_graph(gf_handle* h) {
+  if (h->graph[h->cur]) return GF_OK;
+  GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = GF_OK;
+  for (int j = 0; j < kGraphSweeps && rc == GF_OK; ++j) rc = enqueue_loop_sweep(h, h->cap_stream);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc != GF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph[h->cur], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return GF_OK;
+}
+
+int read_state(gf_handle* h, DevState* out) {
+  GF_CK(h, cudaMemcpyAsync(out, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  GF_CK(h, cudaStreamSynchronize(h->stream));
+  return GF_OK;
+}
+
+// One phase of Algorithm 1 on the current buffer: measure, then sweeps until every
+// unit is below eps or `budget` sweeps were done.  *done receives the sweeps done.
+int run_phase(gf_handle* h, double eps, int budget, int* done) {
+  DevState s{};
+  s.sweep = 0;
+  s.limit = budget;
+  s.check_interval = h->check_interval;
+  s.reunit_interval = h->reunit_interval;
+  s.n_active = 0;
+  s.ticket = 0;
+  s.eps = eps;
+  GF_CK(h, cudaMemcpyAsync(h->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream));
+  int rc = enqueue_measure_all(h, FINISH_RESET);
+  if (rc != GF_OK) return rc;
+  if ((rc = read_state(h, &s)) != GF_OK) return rc;
+  if ((rc = ensure_graph(h)) != GF_OK) return rc;
+  while (s.n_active > 0 && s.sweep < s.limit) {
+    GF_CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+    if ((rc = read_state(h, &s)) != GF_OK) return rc;
+  }
+  *done = s.sweep;
+  return GF_OK;
+}
+
+int copy_out(gf_handle* h, double* F, double* theta, double* uF, double* uT, int* iters) {
+  if (F) GF_CK(h, cudaMemcpyAsync(F, h->d_lF, sizeof(double) * h->n_lat, cudaMemcpyDeviceToHost, h->stream));
+  if (theta) GF_CK(h, cudaMemcpyAsync(theta, h->d_lT, sizeof(double) * h->n_lat, cudaMemcpyDeviceToHost, h->stream));
+  if (uF) GF_CK(h, cudaMemcpyAsync(uF, h->d_uF, sizeof(double) * h->n_units, cudaMemcpyDeviceToHost, h->stream));
+  if (uT) GF_CK(h, cudaMemcpyAsync(uT, h->d_uT, sizeof(double) * h->n_units, cudaMemcpyDeviceToHost, h->stream));
+  if (iters) GF_CK(h, cudaMemcpyAsync(iters, h->d_iters, sizeof(int) * h->n_units, cudaMemcpyDeviceToHost, h->stream));
+  GF_CK(h, cudaStreamSynchronize(h->stream));
+  return GF_OK;
+}
+
+}  // namespace
+
+// ===================================================================================
+// C ABI
+// ===================================================================================
+extern "C" {
+
+int gf_workspace_bytes(int n_lat, const int* dims, int gauge, int storage, int flags, size_t* bytes) {
+  std::string why;
+  if (!bytes) return GF_EINVAL;
+  int rc = check_common(n_lat, dims, gauge, storage, flags, &why);
+  if (rc != GF_OK) return rc;
+  Layout L;
+  plan(n_lat, dims, gauge, storage, flags, &L);
+  *bytes = L.total;
+  return GF_OK;
+}
+
+int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flags, void* stream,
+                    void* workspace, size_t workspace_bytes, gf_handle** out) {
+  if (!out) return GF_EINVAL;
+  *out = nullptr;
+  g_create_error.clear();
+  std::string why;
+  int rc = check_common(n_lat, dims, gauge, storage, flags, &why);
+  if (rc != GF_OK) {
+    g_create_error = why;
+    return rc;
+  }
+  gf_handle* h = new (std::nothrow) gf_handle();
+  if (!h) {
+    g_create_error = "host allocation failed";
+    return GF_ENOMEM;
+  }
+  h->n_lat = n_lat;
+  h->gauge = gauge;
+  h->nd = gauge == GF_LANDAU ? 4 : 3;
+  h->storage = storage;
+  h->flags = (storage == GF_FP64_18) ? (flags & ~GF_FLAG_MIXED) : flags;
+  h->dims.assign(dims, dims + 4 * n_lat);
+  h->stream = (cudaStream_t)stream;
+  plan(n_lat, dims, gauge, storage, h->flags, &h->L);
+  auto bail = [&](int code, const std::string& msg) {
+    g_create_error = msg;
+    gf_destroy(h);
+    return code;
+  };
+  if (workspace) {
+    if (workspace_bytes < h->L.total) return bail(GF_ENOMEM, "workspace smaller than gf_workspace_bytes()");
+    if (((uintptr_t)workspace % 16) != 0) return bail(GF_EINVAL, "workspace must be 16-byte aligned");
+    h->ws = (char*)workspace;
+    h->ws_bytes = workspace_bytes;
+  } else {
+    cudaError_t e = cudaMalloc(&h->ws, h->L.total);
+    if (e != cudaSuccess) {
+      h->ws = nullptr;
+      return bail(GF_ENOMEM, std::string("cudaMalloc of the workspace: ") + cudaGetErrorString(e));
+    }
+    h->own_ws = true;
+    h->ws_bytes = h->L.total;
+  }
+  if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(GF_ECUDA, "cudaStreamCreate failed");
+  const Layout& L = h->L;
+  char* w = h->ws;
+  h->links = w + L.links;
+  h->links64 = L.links64 == (size_t)-1 ? nullptr : w + L.links64;
+  h->staging = w + L.staging;
+  h->d_lats = (LatDev*)(w + L.lats);
+  h->d_lats64 = (LatDev*)(w + L.lats64);
+  h->d_tiles = (int4*)(w + L.tiles);
+  h->d_unit_tiles = (int*)(w + L.unit_tiles);
+  h->d_unit_lat = (int*)(w + L.unit_lat);
+  h->d_active = (int*)(w + L.active);
+  h->d_iters = (int*)(w + L.iters);
+  h->d_partF = (double*)(w + L.partF);
+  h->d_pthe = (double*)(w + L.pthe);
+  h->d_ptho = (double*)(w + L.ptho);
+  h->d_usF = (double*)(w + L.usF);
+  h->d_usT = (double*)(w + L.usT);
+  h->d_uF = (double*)(w + L.uF);
+  h->d_uT = (double*)(w + L.uT);
+  h->d_lF = (double*)(w + L.lF);
+  h->d_lT = (double*)(w + L.lT);
+  h->d_state = (DevState*)(w + L.state);
+  h->n_units = L.n_units;
+
+  long long off = 0, off64 = 0;
+  int unit = 0;
+  for (int l = 0; l < n_lat; ++l) {
+    LatDev d{};
+    for (int k = 0; k < 4; ++k) d.L[k] = dims[4 * l + k];
+    d.V = (long long)d.L[0] * d.L[1] * d.L[2] * d.L[3];
+    d.Vh = (int)(d.V / 2);
+    d.V3h = d.L[0] * d.L[1] * d.L[2] / 2;
+    d.unit0 = unit;
+    d.n_units = gauge == GF_LANDAU ? 1 : d.L[3];
+    unit += d.n_units;
+    d.off_bytes = off;
+    off += d.V * 4 * link_bytes(storage);
+    h->lats.push_back(d);
+    d.off_bytes = off64;
+    off64 += d.V * 4 * 144;
+    h->lats64.push_back(d);
+  }
+  if (cudaMemcpyAsync(h->d_lats, h->lats.data(), sizeof(LatDev) * n_lat, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->d_lats64, h->lats64.data(), sizeof(LatDev) * n_lat, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return bail(GF_ECUDA, "copy of the lattice tables failed");
+  launch_fill_int(h->d_active, 1, h->n_units, h->stream);
+  if (cudaMemsetAsync(h->d_iters, 0, sizeof(int) * h->n_units, h->stream) != cudaSuccess ||
+      cudaGetLastError() != cudaSuccess)
+    return bail(GF_ECUDA, "initialisation of the unit tables failed");
+  if (build_tiles(h) != GF_OK) return bail(GF_ECUDA, h->err);
+  *out = h;
+  return GF_OK;
+}
+
+int gf_create(const int dims[4], int nc, int gauge, int storage, int flags, void* stream, void* workspace,
+              size_t workspace_bytes, gf_handle** out) {
+  if (nc != 3) {
+    g_create_error = "only Nc = 3 (SU(3)) is supported";
+    if (out) *out = nullptr;
+    return GF_EINVAL;
+  }
+  return gf_create_batch(1, dims, gauge, storage, flags, stream, workspace, workspace_bytes, out);
+}
+
+void gf_destroy(gf_handle* h) {
+  if (!h) return;
+  drop_graphs(h);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  delete h;
+}
+
+const char* gf_last_error(const gf_handle* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+int gf_num_lattices(const gf_handle* h) { return h ? h->n_lat : GF_EINVAL; }
+int gf_num_units(const gf_handle* h) { return h ? h->n_units : GF_EINVAL; }
+
+int gf_upload(gf_handle* h, int lat, const double* links, int on_device) {
+  if (!h) return GF_EINVAL;
+  if (lat < 0 || lat >= h->n_lat || !links) return fail(h, GF_EINVAL, "bad lattice index or null buffer");
+  if (on_device && ((uintptr_t)links % 16) != 0) return fail(h, GF_EINVAL, "device buffer must be 16-byte aligned");
+  h->cur = 0;
+  const LatDev& d = h->lats[lat];
+  if (on_device) {
+    launch_pack(h->storage, h->links, d, links, 0, d.V, h->stream);
+    GF_CK_LAUNCH(h);
+  } else {
+    const long long per = (long long)(h->L.staging_bytes / (4 * 144));
+    for (long long s0 = 0; s0 < d.V; s0 += per) {
+      const long long n = std::min(per, d.V - s0);
+      GF_CK(h, cudaMemcpyAsync(h->staging, links + s0 * 4 * 18, (size_t)n * 4 * 144, cudaMemcpyHostToDevice, h->stream));
+      launch_pack(h->storage, h->links, d, (const double*)h->staging, s0, n, h->stream);
+      GF_CK_LAUNCH(h);
+    }
+  }
+  launch_fill_int(h->d_active, 1, h->n_units, h->stream);
+  GF_CK_LAUNCH(h);
+  GF_CK(h, cudaMemsetAsync(h->d_iters, 0, sizeof(int) * h->n_units, h->stream));
+  if (!on_device) GF_CK(h, cudaStreamSynchronize(h->stream));
+  return GF_OK;
+}
+
+int gf_download(gf_handle* h, int lat, double* links, int on_device) {
+  if (!h) return GF_EINVAL;
+  if (lat < 0 || lat >= h->n_lat || !links) return fail(h, GF_EINVAL, "bad lattice index or null buffer");
+  if (on_device && ((uintptr_t)links % 16) != 0) return fail(h, GF_EINVAL, "device buffer must be 16-byte aligned");
+  const LatDev& d = cur_lat_host(h, lat);
+  const int st = cur_storage(h);
+  if (on_device) {
+    launch_unpack(st, cur_links(h), d, links, 0, d.V, h->stream);
+    GF_CK_LAUNCH(h);
+  } else {
+    const long long per = (long long)(h->L.staging_bytes / (4 * 144));
+    for (long long s0 = 0; s0 < d.V; s0 += per) {
+      const long long n = std::min(per, d.V - s0);
+      launch_unpack(st, cur_links(h), d, (double*)h->staging, s0, n, h->stream);
+      GF_CK_LAUNCH(h);
+      GF_CK(h, cudaMemcpyAsync(links + s0 * 4 * 18, h->staging, (size_t)n * 4 * 144, cudaMemcpyDeviceToHost, h->stream));
+    }
+    GF_CK(h, cudaStreamSynchronize(h->stream));
+  }
+  return GF_OK;
+}
+
+int gf_functional_theta(gf_handle* h, double* F, double* theta, double* unit_F, double* unit_theta) {
+  if (!h) return GF_EINVAL;
+  // the finishing kernel needs a valid ticket; the loop fields stay as they are
+  GF_CK(h, cudaMemsetAsync(&h->d_state->ticket, 0, sizeof(unsigned int), h->stream));
+  int rc = enqueue_measure_all(h, FINISH_MEASURE);
+  if (rc != GF_OK) return rc;
+  return copy_out(h, F, theta, unit_F, unit_theta, nullptr);
+}
+
+int gf_or_sweep(gf_handle* h, int parity, double omega) {
+  if (!h) return GF_EINVAL;
+  if (parity < 0 || parity > 2) return fail(h, GF_EINVAL, "parity must be 0, 1 or 2");
+  if (!(omega >= 1.0 && omega < 2.0)) return fail(h, GF_EINVAL, "omega must lie in [1, 2)");
+  const int st = cur_storage(h);
+  for (int p = 0; p < 2; ++p) {
+    if (parity != 2 && p != parity) continue;
+    SweepArgs a = sweep_args(h, p, false);
+    a.omega = omega;
+    launch_sweep(st, h->nd, h->repro, a, h->n_tiles, h->threads, h->stream);
+    GF_CK_LAUNCH(h);
+  }
+  return GF_OK;
+}
+
+int gf_reunitarize(gf_handle* h) {
+  if (!h) return GF_EINVAL;
+  for (int l = 0; l < h->n_lat; ++l) {
+    launch_reunit(cur_storage(h), cur_links(h), cur_lat_host(h, l), h->stream);
+    GF_CK_LAUNCH(h);
+  }
+  return GF_OK;
+}
+
+int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double* theta) {
+  if (!h) return GF_EINVAL;
+  if (!(eps > 0.0) || maxiter < 0) return fail(h, GF_EINVAL, "need eps > 0 and maxiter >= 0");
+  GF_CK(h, cudaMemsetAsync(h->d_iters, 0, sizeof(int) * h->n_units, h->stream));
+  h->phase_sweeps[0] = h->phase_sweeps[1] = 0;
+  int rc, done = 0;
+  const bool mixed = (h->flags & GF_FLAG_MIXED) && h->cur == 0;
+  if (mixed) {
+    if ((rc = run_phase(h, std::max(eps, h->eps_switch), maxiter, &done)) != GF_OK) return rc;
+    h->phase_sweeps[0] = done;
+    for (int l = 0; l < h->n_lat; ++l) {
+      launch_to_fp64(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
+      GF_CK_LAUNCH(h);
+    }
+    h->cur = 1;
+    int done2 = 0;
+    if ((rc = run_phase(h, eps, maxiter - done, &done2)) != GF_OK) return rc;
+    h->phase_sweeps[1] = done2;
+  } else {
+    if ((rc = run_phase(h, eps, maxiter, &done)) != GF_OK) return rc;
+    h->phase_sweeps[h->cur == 1 || h->storage == GF_FP64_18 ? 1 : 0] = done;
+  }
+  if ((rc = copy_out(h, F, theta, nullptr, nullptr, iters)) != GF_OK) return rc;
+  DevState s{};
+  if ((rc = read_state(h, &s)) != GF_OK) return rc;
+  return s.n_active > 0 ? GF_ENOTCONVERGED : GF_OK;
+}
+
+int gf_set_omega(gf_handle* h, double omega) {
+  if (!h) return GF_EINVAL;
+  if (!(omega >= 1.0 && omega < 2.0)) return fail(h, GF_EINVAL, "omega must lie in [1, 2)");
+  if (omega != h->omega) drop_graphs(h);
+  h->omega = omega;
+  return GF_OK;
+}
+
+int gf_set_overrelax_form(gf_handle* h, int form) {
+  if (!h) return GF_EINVAL;
+  if (form != GF_OR_FIRST_ORDER && form != GF_OR_EXACT) return fail(h, GF_EINVAL, "unknown overrelaxation form");
+  if (form != h->form) drop_graphs(h);
+  h->form = form;
+  return GF_OK;
+}
+
+int gf_set_reunit_interval(gf_handle* h, int n) {
+  if (!h) return GF_EINVAL;
+  if (n < 0) return fail(h, GF_EINVAL, "reunit interval must be >= 0");
+  h->reunit_interval = n;
+  return GF_OK;
+}
+
+int gf_set_check_interval(gf_handle* h, int n) {
+  if (!h) return GF_EINVAL;
+  if (n < 1) return fail(h, GF_EINVAL, "check interval must be >= 1");
+  h->check_interval = n;
+  return GF_OK;
+}
+
+int gf_set_mixed_switch(gf_handle* h, double eps_sw) {
+  if (!h) return GF_EINVAL;
+  if (!(eps_sw > 0.0)) return fail(h, GF_EINVAL, "switch threshold must be > 0");
+  h->eps_switch = eps_sw;
+  return GF_OK;
+}
+
+int gf_set_reproducible(gf_handle* h, int on) {
+  if (!h) return GF_EINVAL;
+  if ((on != 0) != h->repro) drop_graphs(h);
+  h->repro = on != 0;
+  return GF_OK;
+}
+
+int gf_set_block_size(gf_handle* h, int threads) {
+  if (!h) return GF_EINVAL;
+  if (threads != 64 && threads != 128 && threads != 256) return fail(h, GF_EINVAL, "block size must be 64, 128 or 256");
+  if (threads == h->threads) return GF_OK;
+  h->threads = threads;
+  return build_tiles(h);
+}
+
+int gf_fix_phase_sweeps(const gf_handle* h, int* fp32_sweeps, int* fp64_sweeps) {
+  if (!h) return GF_EINVAL;
+  if (fp32_sweeps) *fp32_sweeps = h->phase_sweeps[0];
+  if (fp64_sweeps) *fp64_sweeps = h->phase_sweeps[1];
+  return GF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,215 @@
+// gf_inst_common.cu -- the finishing reduction and the element kernels (all storages).
+#include "gf_kernels.cuh"
+
+namespace gf {
+
+__global__ void __launch_bounds__(256) k_finish(FinishArgs a) {
+  __shared__ double red[96];
+  __shared__ int s_last;
+  const int u = blockIdx.x;
+  bool loop = a.mode == FINISH_LOOP;
+  bool check = true;
+  if (loop) {
+    if (!state_running(a.st)) return;  // uniform over the grid: nobody takes a ticket
+    check = state_check_sweep(a.st);
+  }
+  const bool was_active = a.active[u] != 0;
+  const bool reduce = loop ? (was_active && check) : true;
+  if (reduce) {
+    const int tb = a.unit_tiles[u], te = a.unit_tiles[u + 1];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int i = tb + (int)threadIdx.x; i < te; i += blockDim.x) {
+      v[0] += a.part_F[i];
+      v[1] += a.part_th_even[i];
+      v[2] += a.part_th_odd[i];
+    }
+    block_sum<3>(v, red);
+    if (threadIdx.x == 0) {
+      const LatDev lat = a.lats[a.unit_lat[u]];
+      const double vol = a.nd == 4 ? (double)lat.V : 2.0 * lat.V3h;  // Landau: V, Coulomb: slice
+      const double sF = v[0], sTh = v[1] + v[2];
+      a.unit_sumF[u] = sF;
+      a.unit_sumTh[u] = sTh;
+      a.unit_F[u] = sF / ((double)a.nd * 3.0 * vol);
+      a.unit_theta[u] = sTh / (3.0 * vol);
+    }
+  }
+  if (threadIdx.x == 0) {
+    if (loop) {
+      if (was_active) {
+        a.iters[u] += 1;
+        if (check) a.active[u] = a.unit_theta[u] >= a.st->eps;
+      }
+    } else if (a.mode == FINISH_RESET) {
+      a.active[u] = a.unit_theta[u] >= a.st->eps;
+    }
+    __threadfence();
+    const unsigned int t = atomicAdd(&a.st->ticket, 1u);
+    s_last = (t == (unsigned int)(a.n_units - 1));
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last block: lattice totals in a fixed order, active count, loop state
+  if (!loop || check) {
+    for (int l = threadIdx.x; l < a.n_lat; l += blockDim.x) {
+      const LatDev lat = a.lats[l];
+      double sF = 0.0, sTh = 0.0;
+      for (int k = 0; k < lat.n_units; ++k) {
+        sF += __ldcg(a.unit_sumF + lat.unit0 + k);
+        sTh += __ldcg(a.unit_sumTh + lat.unit0 + k);
+      }
+      a.lat_F[l] = sF / ((double)a.nd * 3.0 * (double)lat.V);
+      a.lat_theta[l] = sTh / (3.0 * (double)lat.V);
+    }
+  }
+  double c[1] = {0.0};
+  for (int k = threadIdx.x; k < a.n_units; k += blockDim.x) c[0] += (double)__ldcg(a.active + k);
+  block_sum<1>(c, red);
+  if (threadIdx.x == 0) {
+    if (a.mode != FINISH_MEASURE) a.st->n_active = (int)c[0];
+    if (loop) a.st->sweep += 1;
+    a.st->ticket = 0u;
+  }
+}
+
+void launch_finish(const FinishArgs& a, cudaStream_t s) { k_finish<<<a.n_units, 256, 0, s>>>(a); }
+
+// ---------------------------------------------------------------------------------
+// element kernels
+// ---------------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(256) k_pack(char* links, LatDev lat, const double2* src,
+                                              long long s0, long long nsites) {
+  using St = Store<S>;
+  using T = typename St::T;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= nsites * 4) return;
+  const long long s = s0 + i / 4;
+  const int mu = (int)(i % 4);
+  long long r = s;
+  const int x = (int)(r % lat.L[0]); r /= lat.L[0];
+  const int y = (int)(r % lat.L[1]); r /= lat.L[1];
+  const int z = (int)(r % lat.L[2]);
+  const int t = (int)(r / lat.L[2]);
+  const int p = (x + y + z + t) & 1;
+  const int idx = p * lat.Vh + (int)(s >> 1);
+  cx<T> e[St::NE];
+#pragma unroll
+  for (int k = 0; k < St::NE; ++k) {
+    const double2 v = src[i * 9 + k];
+    e[k] = {(T)v.x, (T)v.y};
+  }
+  St::store(links + lat.off_bytes, lat.V, mu, idx, e);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_unpack(const char* links, LatDev lat, double2* dst,
+                                                long long s0, long long nsites) {
+  using St = Store<S>;
+  using T = typename St::T;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= nsites * 4) return;
+  const long long s = s0 + i / 4;
+  const int mu = (int)(i % 4);
+  long long r = s;
+  const int x = (int)(r % lat.L[0]); r /= lat.L[0];
+  const int y = (int)(r % lat.L[1]); r /= lat.L[1];
+  const int z = (int)(r % lat.L[2]);
+  const int t = (int)(r / lat.L[2]);
+  const int p = (x + y + z + t) & 1;
+  const int idx = p * lat.Vh + (int)(s >> 1);
+  cx<T> e[St::NE];
+  St::load(links + lat.off_bytes, lat.V, mu, idx, e);
+  cx<double> m[9];
+#pragma unroll
+  for (int k = 0; k < St::NE; ++k) m[k] = {(double)e[k].re, (double)e[k].im};
+  if constexpr (St::NE == 6) third_row(m, m + 6);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) dst[i * 9 + k] = make_double2(m[k].re, m[k].im);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_reunit(char* links, LatDev lat) {
+  using St = Store<S>;
+  using T = typename St::T;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 4 * lat.V) return;
+  const int mu = (int)(i / lat.V), idx = (int)(i % lat.V);
+  cx<T> e[St::NE];
+  St::load(links + lat.off_bytes, lat.V, mu, idx, e);
+  reunit(e);
+  St::store(links + lat.off_bytes, lat.V, mu, idx, e);
+}
+
+template <int S>
+__global__ void __launch_bounds__(256) k_to_fp64(const char* src, char* dst, LatDev ls, LatDev ld) {
+  using St = Store<S>;
+  using T = typename St::T;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= 4 * ls.V) return;
+  const int mu = (int)(i / ls.V), idx = (int)(i % ls.V);
+  cx<T> e[St::NE];
+  St::load(src + ls.off_bytes, ls.V, mu, idx, e);
+  cx<double> m[9];
+#pragma unroll
+  for (int k = 0; k < St::NE; ++k) m[k] = {(double)e[k].re, (double)e[k].im};
+  if constexpr (St::NE == 6) third_row(m, m + 6);
+  reunit(m);
+  Store<GF_FP64_18>::store(dst + ld.off_bytes, ld.V, mu, idx, m);
+}
+
+__global__ void k_fill_int(int* p, int value, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = value;
+}
+
+void launch_fill_int(int* p, int value, int n, cudaStream_t s) {
+  if (n > 0) k_fill_int<<<(n + 255) / 256, 256, 0, s>>>(p, value, n);
+}
+
+static unsigned int blocks_for(long long n, int threads) { return (unsigned int)((n + threads - 1) / threads); }
+
+#define GF_ELEM_SWITCH(storage, CALL)                  \
+  switch (storage) {                                   \
+    case GF_FP64_18: CALL(GF_FP64_18); break;          \
+    case GF_FP32_18: CALL(GF_FP32_18); break;          \
+    default: CALL(GF_FP32_12); break;                  \
+  }
+
+void launch_pack(int storage, char* links, const LatDev& lat, const double* src, long long s0,
+                 long long nsites, cudaStream_t s) {
+  if (nsites <= 0) return;
+  const unsigned int nb = blocks_for(nsites * 4, 256);
+  const double2* p = reinterpret_cast<const double2*>(src);
+#define GF_CALL(S) k_pack<S><<<nb, 256, 0, s>>>(links, lat, p, s0, nsites)
+  GF_ELEM_SWITCH(storage, GF_CALL)
+#undef GF_CALL
+}
+
+void launch_unpack(int storage, const char* links, const LatDev& lat, double* dst, long long s0,
+                   long long nsites, cudaStream_t s) {
+  if (nsites <= 0) return;
+  const unsigned int nb = blocks_for(nsites * 4, 256);
+  double2* p = reinterpret_cast<double2*>(dst);
+#define GF_CALL(S) k_unpack<S><<<nb, 256, 0, s>>>(links, lat, p, s0, nsites)
+  GF_ELEM_SWITCH(storage, GF_CALL)
+#undef GF_CALL
+}
+
+void launch_reunit(int storage, char* links, const LatDev& lat, cudaStream_t s) {
+  const unsigned int nb = blocks_for(4 * lat.V, 256);
+#define GF_CALL(S) k_reunit<S><<<nb, 256, 0, s>>>(links, lat)
+  GF_ELEM_SWITCH(storage, GF_CALL)
+#undef GF_CALL
+}
+
+void launch_to_fp64(int storage, const char* src, char* dst, const LatDev& ls, const LatDev& ld,
+                    cudaStream_t s) {
+  const unsigned int nb = blocks_for(4 * ls.V, 256);
+#define GF_CALL(S) k_to_fp64<S><<<nb, 256, 0, s>>>(src, dst, ls, ld)
+  GF_ELEM_SWITCH(storage, GF_CALL)
+#undef GF_CALL
+}
+
+}  // namespace gf

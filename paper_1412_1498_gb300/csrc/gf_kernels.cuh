@@ -1,0 +1,387 @@
+// gf_kernels.cuh -- the kernels of libgf, templated on storage and gauge.
+//
+// Instantiated in exactly one translation unit each (gf_inst_*.cu); see the bottom of
+// this file for the launch helpers declared to the host code.
+#pragma once
+
+#include "gf_device.cuh"
+
+namespace gf {
+
+// ----------------------------------------------------------------------------------
+// Eqs. (4)-(6): maximise Re Tr[R K] in the SU(2) subgroup on rows/columns (i, j),
+// then R -> R^omega (Section 1, sentence after Eq. (6); Mandula-Ogilvie).
+//   alpha = K_ii + conj(K_jj), beta = K_ji - conj(K_ij): Re Tr[R K] = const +
+//   Re(a alpha) + Re(b beta) for R|_(i,j) = [[a, b], [-conj b, conj a]], maximal at
+//   (a, b) = conj(alpha, beta) / |(alpha, beta)|; R = 1 when alpha = beta = 0.
+// REPRO: IEEE divisions in the order of a plain C implementation; otherwise one
+// reciprocal square root and multiplications.
+// ----------------------------------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T gf_rsqrt(T x);
+template <>
+__device__ __forceinline__ double gf_rsqrt<double>(double x) { return rsqrt(x); }
+template <>
+__device__ __forceinline__ float gf_rsqrt<float>(float x) { return rsqrtf(x); }
+
+template <class T, bool REPRO>
+__device__ __forceinline__ void su2_maximiser(const cx<T> (&K)[9], int i, int j, T omega,
+                                              int form, cx<T>& a, cx<T>& b) {
+  const cx<T> alpha = cadd(K[3 * i + i], cconj(K[3 * j + j]));
+  const cx<T> beta = csub(K[3 * j + i], cconj(K[3 * i + j]));
+  const T n2 = ((alpha.re * alpha.re + alpha.im * alpha.im) + beta.re * beta.re) + beta.im * beta.im;
+  a = {T(1), T(0)};
+  b = {T(0), T(0)};
+  if constexpr (REPRO) {
+    const T n = gf_sqrt(n2);
+    if (n > T(0)) {
+      a = {alpha.re / n, -alpha.im / n};
+      b = {beta.re / n, -beta.im / n};
+    }
+  } else {
+    if (n2 > T(0)) {
+      const T rn = gf_rsqrt(n2);
+      a = {alpha.re * rn, -alpha.im * rn};
+      b = {beta.re * rn, -beta.im * rn};
+    }
+  }
+  if (form == GF_OR_FIRST_ORDER) {
+    // g^omega to first order: 1 + omega (g - 1), renormalised onto SU(2)
+    const cx<T> a1 = {(T(1) - omega) + omega * a.re, omega * a.im};
+    const cx<T> b1 = {omega * b.re, omega * b.im};
+    const T m2 = ((a1.re * a1.re + a1.im * a1.im) + b1.re * b1.re) + b1.im * b1.im;
+    if constexpr (REPRO) {
+      const T m = gf_sqrt(m2);
+      if (m > T(0)) {
+        a = {a1.re / m, a1.im / m};
+        b = {b1.re / m, b1.im / m};
+      }
+    } else {
+      if (m2 > T(0)) {
+        const T rm = gf_rsqrt(m2);
+        a = cscale(a1, rm);
+        b = cscale(b1, rm);
+      }
+    }
+  } else {
+    // exact power: R = cos(phi) + i sin(phi) n.sigma  ->  cos(omega phi) + i sin(omega phi) n.sigma
+    const T s = gf_sqrt((a.im * a.im + b.re * b.re) + b.im * b.im);
+    if (s > T(0)) {
+      const T phi = atan2(s, a.re);
+      const T c1 = cos(omega * phi), s1 = sin(omega * phi);
+      a = {c1, (a.im / s) * s1};
+      b = {(b.re / s) * s1, (b.im / s) * s1};
+    }
+  }
+}
+
+// M <- R M for the subgroup element R on rows (i, j)
+template <class T>
+__device__ __forceinline__ void su2_left_mul(cx<T> (&M)[9], int i, int j, cx<T> a, cx<T> b) {
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const cx<T> mi = M[3 * i + c], mj = M[3 * j + c];
+    M[3 * i + c] = cadd(cmul(a, mi), cmul(b, mj));
+    M[3 * j + c] = cadd(cmul(cneg(cconj(b)), mi), cmul(cconj(a), mj));
+  }
+}
+
+// G = product of the three subgroup maximisers for K (Cabibbo-Marinari order (0,1),
+// (0,2), (1,2)), K rotated after each one.
+template <class T, bool REPRO>
+__device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega, int form) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) G[e] = {T(0), T(0)};
+  G[0] = G[4] = G[8] = {T(1), T(0)};
+  cx<T> a, b;
+  su2_maximiser<T, REPRO>(K, 0, 1, omega, form, a, b);
+  su2_left_mul(K, 0, 1, a, b);
+  su2_left_mul(G, 0, 1, a, b);
+  su2_maximiser<T, REPRO>(K, 0, 2, omega, form, a, b);
+  su2_left_mul(K, 0, 2, a, b);
+  su2_left_mul(G, 0, 2, a, b);
+  su2_maximiser<T, REPRO>(K, 1, 2, omega, form, a, b);
+  su2_left_mul(K, 1, 2, a, b);
+  su2_left_mul(G, 1, 2, a, b);
+}
+
+// K += U_mu(x) + U_mu(x - mu)^dagger (in-place form of Eq. (5))
+template <class T, int NE>
+__device__ __forceinline__ void add_to_K(cx<T> (&K)[9], const cx<T> (&f)[NE], const cx<T> (&b)[NE]) {
+  cx<T> fu[9], bu[9];
+  to_full(f, fu);
+  to_full(b, bu);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) K[3 * r + c] = cadd(K[3 * r + c], cadd(fu[3 * r + c], cconj(bu[3 * c + r])));
+}
+
+// A += U_nu(x - nu) - U_nu(x)  (Eq. (3), one direction)
+template <class T, int NE>
+__device__ __forceinline__ void add_to_A(cx<T> (&A)[9], const cx<T> (&f)[NE], const cx<T> (&b)[NE]) {
+  cx<T> fu[9], bu[9];
+  to_full(f, fu);
+  to_full(b, bu);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) A[e] = cadd(A[e], csub(bu[e], fu[e]));
+}
+
+// Tr[Delta Delta^dagger] with Delta = A - A^dagger - (1/3) Tr(A - A^dagger)
+template <class T>
+__device__ __forceinline__ double theta_site(const cx<T> (&A)[9]) {
+  cx<T> D[9];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) D[3 * i + j] = csub(A[3 * i + j], cconj(A[3 * j + i]));
+  const cx<T> sum = cadd(cadd(D[0], D[4]), D[8]);
+  const cx<T> tr = {sum.re / T(3), sum.im / T(3)};
+  D[0] = csub(D[0], tr);
+  D[4] = csub(D[4], tr);
+  D[8] = csub(D[8], tr);
+  T q = T(0);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) q = q + (D[e].re * D[e].re + D[e].im * D[e].im);
+  return (double)q;
+}
+
+// ----------------------------------------------------------------------------------
+// Kernel arguments
+// ----------------------------------------------------------------------------------
+struct SweepArgs {
+  char* links;
+  const LatDev* lats;
+  const int4* tiles;       // (lat, t, first h3, unit) per block
+  const int* active;       // per unit (nullable: all active)
+  const DevState* st;      // nullable; when set, the loop state decides everything
+  double* part_theta;      // per tile: theta partial of the updated (odd) sites
+  int parity;
+  int form;
+  int reunit;              // used when st == nullptr
+  int measure;             // used when st == nullptr
+  double omega;
+};
+
+struct MeasureArgs {
+  const char* links;
+  const LatDev* lats;
+  const int4* tiles;
+  const int* active;       // nullable
+  const DevState* st;      // nullable; when set, only runs on check sweeps
+  double* part_F;          // nullable: per tile sum of Re Tr over the 2 nd links of each site
+  double* part_theta;      // per tile sum of Tr[Delta Delta^+]
+  int parity;
+};
+
+struct FinishArgs {
+  const LatDev* lats;
+  const int* unit_tiles;   // n_units + 1 tile boundaries
+  const int* unit_lat;     // lattice of each unit
+  int* active;
+  int* iters;
+  const double* part_F;
+  const double* part_th_even;
+  const double* part_th_odd;
+  double* unit_sumF;
+  double* unit_sumTh;
+  double* unit_F;
+  double* unit_theta;
+  double* lat_F;
+  double* lat_theta;
+  DevState* st;
+  int n_units;
+  int n_lat;
+  int nd;
+  int mode;                // FINISH_LOOP, FINISH_MEASURE, FINISH_RESET
+};
+
+enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2 };
+
+// ----------------------------------------------------------------------------------
+// Algorithm 1, one half-sweep: every site of one parity, one thread per site.
+// KEEP: hold the 8 links in registers (FP32); otherwise stream them twice (FP64).
+// ----------------------------------------------------------------------------------
+template <int S, int ND, bool REPRO>
+__global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  constexpr int NE = St::NE;
+  constexpr bool KEEP = sizeof(T) == 4;
+  __shared__ double red[32];
+
+  bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
+  if (a.st) {
+    if (!state_running(a.st)) return;
+    reunit_now = a.parity == 1 && state_reunit_sweep(a.st);
+    measure_now = a.parity == 1 && state_check_sweep(a.st);
+  }
+  const int4 tile = a.tiles[blockIdx.x];
+  if (a.active && !a.active[tile.w]) return;
+  const LatDev lat = a.lats[tile.x];
+  const int h3 = tile.z + (int)threadIdx.x;
+  double q = 0.0;
+  if (h3 < lat.V3h) {
+    const int p = a.parity;
+    const int h = tile.y * lat.V3h + h3;
+    const Site s = site_of(lat, p, h);
+    char* base = a.links + lat.off_bytes;
+    const long long V = lat.V;
+    const int idx_f = p * lat.Vh + h;
+    int idx_b[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) idx_b[mu] = (1 - p) * lat.Vh + (int)(back_lexi(lat, s, mu) >> 1);
+    const T omega = (T)a.omega;
+
+    cx<T> K[9], G[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) K[e] = {T(0), T(0)};
+
+    if constexpr (KEEP) {
+      cx<T> f[4][NE], b[4][NE];
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        St::load(base, V, mu, idx_f, f[mu]);
+        St::load(base, V, mu, idx_b[mu], b[mu]);
+      }
+#pragma unroll
+      for (int mu = 0; mu < ND; ++mu) add_to_K(K, f[mu], b[mu]);
+      su3_update<T, REPRO>(K, G, omega, a.form);
+      cx<T> A[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        left_mul(G, f[mu]);
+        right_mul_dag(b[mu], G);
+        if (reunit_now) {
+          reunit(f[mu]);
+          reunit(b[mu]);
+        }
+        if (mu < ND && measure_now) add_to_A(A, f[mu], b[mu]);
+        St::store(base, V, mu, idx_f, f[mu]);
+        St::store(base, V, mu, idx_b[mu], b[mu]);
+      }
+      if (measure_now) q = theta_site(A);
+    } else {
+#pragma unroll
+      for (int mu = 0; mu < ND; ++mu) {
+        cx<T> f[NE], b[NE];
+        St::load(base, V, mu, idx_f, f);
+        St::load(base, V, mu, idx_b[mu], b);
+        add_to_K(K, f, b);
+      }
+      su3_update<T, REPRO>(K, G, omega, a.form);
+      cx<T> A[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {
+        cx<T> f[NE], b[NE];
+        St::load(base, V, mu, idx_f, f);
+        St::load(base, V, mu, idx_b[mu], b);
+        left_mul(G, f);
+        right_mul_dag(b, G);
+        if (reunit_now) {
+          reunit(f);
+          reunit(b);
+        }
+        if (mu < ND && measure_now) add_to_A(A, f, b);
+        St::store(base, V, mu, idx_f, f);
+        St::store(base, V, mu, idx_b[mu], b);
+      }
+      if (measure_now) q = theta_site(A);
+    }
+  }
+  if (measure_now) {
+    double v[1] = {q};
+    block_sum<1>(v, red);
+    if (threadIdx.x == 0) a.part_theta[blockIdx.x] = v[0];
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// Eqs. (1)-(3) over the sites of one parity: Re Tr of their 2 nd links (every link is
+// one site's forward or backward link, so parity 0 alone covers all of F) and
+// Tr[Delta Delta^+] of Delta(x) at each site.
+// ----------------------------------------------------------------------------------
+template <int S, int ND>
+__global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  constexpr int NE = St::NE;
+  __shared__ double red[64];
+  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st))) return;
+  const int4 tile = a.tiles[blockIdx.x];
+  if (a.active && !a.active[tile.w]) return;
+  const LatDev lat = a.lats[tile.x];
+  const int h3 = tile.z + (int)threadIdx.x;
+  double fsum = 0.0, q = 0.0;
+  if (h3 < lat.V3h) {
+    const int p = a.parity;
+    const int h = tile.y * lat.V3h + h3;
+    const Site s = site_of(lat, p, h);
+    const char* base = a.links + lat.off_bytes;
+    const int idx_f = p * lat.Vh + h;
+    cx<T> A[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
+    T fs = T(0);
+#pragma unroll
+    for (int nu = 0; nu < ND; ++nu) {
+      cx<T> f[NE], b[NE];
+      St::load(base, lat.V, nu, idx_f, f);
+      St::load(base, lat.V, nu, (1 - p) * lat.Vh + (int)(back_lexi(lat, s, nu) >> 1), b);
+      fs = fs + (re_trace(f) + re_trace(b));
+      add_to_A(A, f, b);
+    }
+    fsum = (double)fs;
+    q = theta_site(A);
+  }
+  double v[2] = {fsum, q};
+  block_sum<2>(v, red);
+  if (threadIdx.x == 0) {
+    if (a.part_F) a.part_F[blockIdx.x] = v[0];
+    a.part_theta[blockIdx.x] = v[1];
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// Per-unit F / theta from the tile partials (fixed order), masks, iteration counts,
+// lattice totals and the loop state.  One block per unit; the last block to finish
+// does the lattice totals (deterministic: fixed summation order everywhere).
+// ----------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_finish(FinishArgs a);
+
+// ----------------------------------------------------------------------------------
+// Element kernels over all links: layout conversion, reunitarisation, FP32 -> FP64.
+// ----------------------------------------------------------------------------------
+// canonical (site-major complex128) -> storage, for sites [s0, s0 + nsites)
+template <int S>
+__global__ void k_pack(char* links, LatDev lat, const double2* src, long long s0, long long nsites);
+// storage -> canonical
+template <int S>
+__global__ void k_unpack(const char* links, LatDev lat, double2* dst, long long s0, long long nsites);
+// reunitarise every link of one lattice
+template <int S>
+__global__ void k_reunit(char* links, LatDev lat);
+// FP32 storage -> FP64-18 storage of the same lattice with an FP64 reunitarisation
+template <int S>
+__global__ void k_to_fp64(const char* src, char* dst, LatDev lat_src, LatDev lat_dst);
+
+// ----------------------------------------------------------------------------------
+// Host-side launchers (defined in the instantiation units)
+// ----------------------------------------------------------------------------------
+void launch_sweep(int storage, int nd, bool repro, const SweepArgs& a, int n_tiles, int threads,
+                  cudaStream_t s);
+void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_finish(const FinishArgs& a, cudaStream_t s);
+void launch_pack(int storage, char* links, const LatDev& lat, const double* src, long long s0,
+                 long long nsites, cudaStream_t s);
+void launch_unpack(int storage, const char* links, const LatDev& lat, double* dst, long long s0,
+                   long long nsites, cudaStream_t s);
+void launch_reunit(int storage, char* links, const LatDev& lat, cudaStream_t s);
+void launch_to_fp64(int storage, const char* src, char* dst, const LatDev& lat_src,
+                    const LatDev& lat_dst, cudaStream_t s);
+
+}  // namespace gf

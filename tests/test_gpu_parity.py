@@ -1,0 +1,268 @@
+"""CUDA path against the CPU oracle, through the C ABI (needs a GB300).
+
+Tolerances:
+  - layout conversion: bit-exact (FP64) / exact FP32 rounding.
+  - F, theta of the same field: 1e-12 relative in FP64.
+  - FP64 sweeps, fused multiply-add allowed: per link 1e-13 after one half-sweep and
+    1e-10 after 100 sweeps (same parity order).
+  - FP64 sweeps in reproducible mode: bit-exact (same IEEE operations in the same order).
+  - FP32 storage: per link 5e-6 after one sweep, 1e-3 after 20 (derived in the design
+    notes from FP32 rounding of ~2e3 operations per site update); F 1e-5 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_1498_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+# several tiles per time slice with a ragged tail at 128 threads: V3h = 10*8*6/2 = 240
+DIMS = (10, 8, 6, 4)
+DIMS_C = (6, 4, 6, 8)
+
+
+@pytest.fixture(scope="module")
+def gf():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1412_1498_gb300 import build
+    build.build()
+    from paper_1412_1498_gb300 import gf as m
+    return m
+
+
+def make(gf, dims, gauge, storage, mixed=False, repro=False):
+    fx = gf.GaugeFixer(dims, gauge, storage, mixed=mixed)
+    if repro:
+        gf.gf_set_reproducible(fx.h, True)
+    return fx
+
+
+def nd_of(gauge):
+    return 4 if gauge == oracle.LANDAU else 3
+
+
+# ---------------------------------------------------------------- layout conversion
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_upload_download_roundtrip(gf, storage):
+    U = fields.random_gauge_config(DIMS, 0.5, 41)
+    fx = make(gf, DIMS, gf.GF_LANDAU, storage)
+    fx.upload(U)
+    got = fx.download()
+    if storage == gf.GF_FP64_18:
+        assert np.array_equal(got, U)
+    else:
+        r = U.astype(np.complex64).astype(np.complex128)
+        if storage == gf.GF_FP32_18:
+            assert np.array_equal(got, r)
+        else:
+            assert np.array_equal(got[..., :2, :], r[..., :2, :])
+            assert np.abs(got[..., 2, :] - U[..., 2, :]).max() < 2e-6
+    # device source and destination
+    Ud = torch.from_numpy(U).cuda()
+    fx.upload(Ud)
+    outd = torch.empty_like(Ud)
+    fx.download(out=outd)
+    torch.cuda.synchronize()
+    assert np.array_equal(outd.cpu().numpy(), got)
+    fx.close()
+
+
+# ---------------------------------------------------------------- Eqs. (1)-(3)
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_functional_theta_matches_oracle(gf, gauge, storage):
+    dims = DIMS if gauge == 0 else DIMS_C
+    U = fields.random_gauge_config(dims, 0.5, 42)
+    fx = make(gf, dims, gauge, storage)
+    fx.upload(U)
+    F, th, uF, uT = fx.functional_theta()
+    V = fx.download()  # the field as stored (rounded for FP32)
+    rF, rth, rFt, rtht = oracle.measure(V, gauge)
+    tol = 1e-12 if storage == gf.GF_FP64_18 else 1e-5
+    assert abs(F[0] - rF) <= tol * abs(rF) and abs(th[0] - rth) <= tol * rth
+    if gauge == oracle.COULOMB:
+        assert np.allclose(uF, rFt, rtol=tol, atol=0) and np.allclose(uT, rtht, rtol=tol, atol=0)
+    else:
+        assert abs(uF[0] - rF) <= tol * abs(rF) and abs(uT[0] - rth) <= tol * rth
+    fx.close()
+
+
+# ---------------------------------------------------------------- Algorithm 1, FP64
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("repro", [False, True])
+def test_half_sweeps_fp64(gf, gauge, form, repro):
+    dims = DIMS if gauge == 0 else DIMS_C
+    U = fields.random_gauge_config(dims, 0.5, 43)
+    ref = U.copy()
+    fx = make(gf, dims, gauge, gf.GF_FP64_18, repro=repro)
+    gf.gf_set_overrelax_form(fx.h, form)
+    fx.upload(U)
+    for parity in (0, 1, 0):
+        gf.gf_or_sweep(fx.h, parity, 1.7)
+        oracle.or_half_sweep(ref, parity, 1.7, gauge, form)
+        got = fx.download()
+        err = np.abs(got - ref).max()
+        if repro and form == 0:
+            assert np.array_equal(got, ref), err
+        else:
+            assert err < 1e-13, err
+    fx.close()
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("repro", [False, True])
+def test_100_sweeps_fp64(gf, gauge, repro):
+    dims = DIMS if gauge == 0 else DIMS_C
+    U = fields.random_gauge_config(dims, 0.5, 44)
+    ref = U.copy()
+    r = oracle.fix(ref, 1e-300, 100, 1.7, gauge, per_slice=False)
+    fx = make(gf, dims, gauge, gf.GF_FP64_18, repro=repro)
+    fx.upload(U)
+    # a single unit per lattice for Coulomb too: stop rule on the total (eps tiny anyway)
+    out = fx.fix(1e-300, 100)
+    got = fx.download()
+    assert np.all(out["iters"] == 100) and out["rc"] == gf.GF_ENOTCONVERGED
+    err = np.abs(got - ref).max()
+    if repro:
+        assert np.array_equal(got, ref), err
+        assert abs(out["F"][0] - r["F"]) <= 1e-12 * abs(r["F"])
+        assert abs(out["theta"][0] - r["theta"]) <= 1e-12 * r["theta"]
+    else:
+        assert err < 1e-10, err
+        assert abs(out["F"][0] - r["F"]) <= 1e-12 * abs(r["F"])
+        assert abs(out["theta"][0] - r["theta"]) <= 1e-8 * r["theta"]
+    fx.close()
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_fix_matches_oracle_run(gf, gauge):
+    # the 8^4 workload (eps 0.4, seeds 1 / 2, omega 1.7, theta < 1e-12 or 500 sweeps)
+    dims = (8, 8, 8, 8)
+    U = fields.random_gauge_config(dims, 0.4, 1, 2)
+    ref = U.copy()
+    r = oracle.fix(ref, 1e-12, 500, 1.7, gauge)
+    fx = make(gf, dims, gauge, gf.GF_FP64_18, repro=True)
+    fx.upload(U)
+    out = fx.fix(1e-12, 500)
+    got = fx.download()
+    assert out["rc"] == gf.GF_OK
+    if gauge == oracle.LANDAU:
+        assert out["iters"][0] == r["iters"]
+    else:
+        assert np.array_equal(out["iters"], r["slice_iters"])
+    assert np.array_equal(got, ref)
+    assert abs(out["F"][0] - r["F"]) <= 1e-12 * abs(r["F"])
+    assert abs(out["theta"][0] - r["theta"]) <= 1e-12 * r["theta"]
+    fx.close()
+
+
+# ---------------------------------------------------------------- FP32 storage
+@pytest.mark.parametrize("storage", [1, 2])
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_fp32_sweeps_against_fp64_oracle(gf, storage, gauge):
+    dims = DIMS if gauge == 0 else DIMS_C
+    U = fields.random_gauge_config(dims, 0.5, 45)
+    fx = make(gf, dims, gauge, storage)
+    fx.upload(U)
+    ref = fx.download()  # start the oracle from the rounded field
+    gf.gf_set_reunit_interval(fx.h, 20)
+    errs = []
+    for k in range(20):
+        gf.gf_or_sweep(fx.h, 2, 1.7)
+        oracle.sweep(ref, 1.7, gauge)
+        if k in (0, 19):
+            errs.append(np.abs(fx.download() - ref).max())
+    assert errs[0] < 5e-6, errs
+    assert errs[1] < 1e-3, errs
+    F, th, _, _ = fx.functional_theta()
+    rF, rth, _, _ = oracle.measure(ref, gauge)
+    assert abs(F[0] - rF) < 1e-5 * abs(rF)
+    fx.close()
+
+
+def test_mixed_precision_reaches_1e15(gf):
+    dims = (8, 8, 8, 8)
+    U = fields.random_gauge_config(dims, 0.4, 1, 2)
+    ref = U.copy()
+    r = oracle.fix(ref, 1e-15, 3000, 1.7)
+    fx = make(gf, dims, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True)
+    fx.upload(U)
+    out = fx.fix(1e-15, 3000)
+    assert out["rc"] == gf.GF_OK
+    n32, n64 = out["phase_sweeps"]
+    assert n32 > 0 and n64 > 0 and n32 + n64 == out["iters"][0]
+    got = fx.download()
+    F, th, _, _ = oracle.measure(got)
+    assert th < 1e-15 * (1 + 1e-6)
+    assert abs(out["theta"][0] - th) <= 1e-9 * th
+    # FP32 storage rounds the field off its gauge orbit at the 1e-7 level (the plaquette
+    # moves), so the maximum reached differs from the FP64 oracle's by that order
+    from tests import obs
+    dplaq = np.abs(obs.plaquettes(got) - obs.plaquettes(U)).max()
+    assert dplaq < 2e-6, dplaq
+    assert abs(F - r["F"]) < 1e-6, abs(F - r["F"])
+    fx.close()
+
+
+# ---------------------------------------------------------------- batches
+def test_batch_equals_each_lattice_alone(gf):
+    dims_list = [(4, 4, 4, 4), (6, 4, 4, 8), (8, 8, 6, 4)]
+    fields_in = [fields.random_gauge_config(d, 0.5, 60 + i) for i, d in enumerate(dims_list)]
+    fb = gf.GaugeFixer(dims_list, gf.GF_LANDAU, gf.GF_FP64_18)
+    gf.gf_set_reproducible(fb.h, True)
+    for i, U in enumerate(fields_in):
+        fb.upload(U, i)
+    ob = fb.fix(1e-12, 400)
+    for i, (d, U) in enumerate(zip(dims_list, fields_in)):
+        fa = make(gf, d, gf.GF_LANDAU, gf.GF_FP64_18, repro=True)
+        fa.upload(U)
+        oa = fa.fix(1e-12, 400)
+        assert oa["iters"][0] == ob["iters"][i]
+        assert np.array_equal(fa.download(), fb.download(i))
+        assert oa["F"][0] == ob["F"][i] and oa["theta"][0] == ob["theta"][i]
+        fa.close()
+    fb.close()
+
+
+# ---------------------------------------------------------------- edge cases
+def test_edge_cases(gf):
+    dims = (2, 2, 2, 2)
+    U = fields.random_gauge_config(dims, 0.5, 70)
+    ref = U.copy()
+    fx = make(gf, dims, gf.GF_LANDAU, gf.GF_FP64_18, repro=True)
+    fx.upload(U)
+    out = fx.fix(1e-300, 5)
+    oracle.fix(ref, 1e-300, 5, 1.7)
+    assert np.array_equal(fx.download(), ref)
+    # maxiter 0 and an already-converged field: no sweep
+    fx.upload(U)
+    out = fx.fix(1e-300, 0)
+    assert out["iters"][0] == 0 and out["rc"] == gf.GF_ENOTCONVERGED
+    assert np.array_equal(fx.download(), U)
+    out = fx.fix(1e9, 10)
+    assert out["iters"][0] == 0 and out["rc"] == gf.GF_OK
+    with pytest.raises(gf.GFError):
+        gf.gf_or_sweep(fx.h, 3, 1.7)
+    with pytest.raises(gf.GFError):
+        gf.gf_or_sweep(fx.h, 0, 2.0)
+    with pytest.raises(gf.GFError):
+        gf.gf_set_block_size(fx.h, 96)
+    fx.close()
+
+
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_block_sizes_agree(gf, threads):
+    U = fields.random_gauge_config(DIMS, 0.5, 71)
+    outs = []
+    for t in (128, threads):
+        fx = make(gf, DIMS, gf.GF_LANDAU, gf.GF_FP64_18, repro=True)
+        gf.gf_set_block_size(fx.h, t)
+        fx.upload(U)
+        o = fx.fix(1e-300, 10)
+        outs.append((fx.download(), o["F"][0]))
+        fx.close()
+    assert np.array_equal(outs[0][0], outs[1][0])
