@@ -199,11 +199,12 @@ def test_mixed_precision_reaches_1e15(gf):
     F, th, _, _ = oracle.measure(got)
     assert th < 1e-15 * (1 + 1e-6)
     assert abs(out["theta"][0] - th) <= 1e-9 * th
-    # FP32 storage rounds the field off its gauge orbit at the 1e-7 level (the plaquette
-    # moves), so the maximum reached differs from the FP64 oracle's by that order
+    # Each FP32 sweep rounds the links off their gauge orbit by ~1e-7 (non-gauge noise
+    # that accumulates like a random walk over the FP32 sweeps), so plaquettes move by
+    # about 1e-7 * sqrt(n32) and the maximum reached differs from the FP64 oracle's
     from tests import obs
     dplaq = np.abs(obs.plaquettes(got) - obs.plaquettes(U)).max()
-    assert dplaq < 2e-6, dplaq
+    assert dplaq < 1e-6 * np.sqrt(n32) + 2e-6, (dplaq, n32)
     assert abs(F - r["F"]) < 1e-6, abs(F - r["F"])
     fx.close()
 
