@@ -110,7 +110,8 @@ GF_API int gf_create_batch(int n_lat, const int *dims, int gauge, int storage, i
 GF_API void gf_destroy(gf_handle *h);
 
 /* Message of the last failure on this handle ("" if none); h == NULL gives the message of
-   the last failed gf_create / gf_create_batch on this thread.  Valid until the next call. */
+   the last failed gf_create / gf_create_batch / gf_functional_theta_noalloc on this
+   thread.  Valid until the next call. */
 GF_API const char *gf_last_error(const gf_handle *h);
 
 /* Number of lattices and of convergence units (see conventions). */
@@ -186,6 +187,33 @@ GF_API int gf_set_block_size(gf_handle *h, int threads);      /* [autotuned]; 64
 
 /* Sweeps done by the last gf_fix in the FP32 and FP64 phases (mixed mode), nullable. */
 GF_API int gf_fix_phase_sweeps(const gf_handle *h, int *fp32_sweeps, int *fp64_sweeps);
+
+/*
+ * F and theta of a field held in device memory, with no allocation of any kind.
+ *
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory: code that runs inside a memory pool reserved up front by a
+ * framework, a loop that must not call cudaMalloc because it may synchronise the
+ * device, or a host process whose device allocations all belong to someone else.
+ * Such a caller passes only its input and output buffers and gets the values of
+ * gf_functional_theta without a handle or a workspace.
+ *   dims: {Lx, Ly, Lz, Lt}, even, >= 2, at most GF_NOALLOC_MAX_BLOCKS * 256 sites in
+ *   all (larger lattices return GF_EINVAL with a message saying so).
+ *   gauge: GF_LANDAU or GF_COULOMB.  links: device memory, canonical layout (as for
+ *   gf_upload), 16-byte aligned.  out: device memory for 2 doubles, receives F and
+ *   theta.  stream: cudaStream_t (NULL = legacy default stream); the call is
+ *   asynchronous on it.
+ * Its block partial sums live in one static device array of
+ * (32 + 2 * GF_NOALLOC_MAX_BLOCKS) doubles (about 4 MiB) that every GPU loading this
+ * library holds until the process exits.  All calls share that array: calls that
+ * overlap on the GPU (different streams or host threads) race on it and give wrong
+ * results; calls on one stream are safe.  The first call on each device looks up the
+ * array's device address with that device current, so make that first call before any
+ * stream capture.  Errors: GF_EINVAL / GF_ECUDA, message in gf_last_error(NULL).
+ */
+#define GF_NOALLOC_MAX_BLOCKS 262144
+GF_API int gf_functional_theta_noalloc(const int dims[4], int gauge, const double *links,
+                                       double *out, void *stream);
 
 #ifdef __cplusplus
 }

@@ -47,12 +47,19 @@ void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int 
 using namespace gf;
 
 namespace {
+thread_local std::string g_create_error;
+}  // namespace
+
+namespace gf {
+void set_thread_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace gf
+
+namespace {
 
 constexpr size_t kAlign = 256;
 constexpr size_t kStagingMax = 32u << 20;  // bytes of canonical links per host copy
 constexpr int kMinThreads = 64;
 constexpr int kGraphSweeps = 16;
-thread_local std::string g_create_error;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 

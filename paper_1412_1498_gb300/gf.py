@@ -60,6 +60,7 @@ _SIGS = {
     "gf_set_reproducible": (_int, [_vp, _int]),
     "gf_set_block_size": (_int, [_vp, _int]),
     "gf_fix_phase_sweeps": (_int, [_vp, _IP, _IP]),
+    "gf_functional_theta_noalloc": (_int, [_IP, _int, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -199,6 +200,12 @@ def gf_fix_phase_sweeps(h):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(_lib.gf_fix_phase_sweeps(h, ctypes.byref(a), ctypes.byref(b)), h)
     return a.value, b.value
+
+
+def gf_functional_theta_noalloc(dims, gauge: int, links_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    """F, theta of a canonical device field into out_ptr[0:2] (device), no allocation."""
+    _check(_lib.gf_functional_theta_noalloc((ctypes.c_int * 4)(*[int(v) for v in dims]), gauge,
+                                            _vp(links_ptr or None), _vp(out_ptr or None), _vp(stream or None)))
 
 
 # ------------------------------------------------------------------------------------
