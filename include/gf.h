@@ -183,7 +183,17 @@ GF_API int gf_set_mixed_switch(gf_handle *h, double eps_sw);  /* [1e-8], > 0    
 GF_API int gf_set_reproducible(gf_handle *h, int on);         /* [0]; 1 = FP64 kernels without
                                   fused multiply-add and with IEEE divisions, in the
                                   oracle's operation order (bit-reproducible results) */
-GF_API int gf_set_block_size(gf_handle *h, int threads);      /* [autotuned]; 64, 128 or 256  */
+GF_API int gf_set_block_size(gf_handle *h, int threads);      /* [128]; 64, 128 or 256        */
+
+/* Half-sweep kernel for FP32-12 storage: GF_SWEEP_REGISTER holds each site's 8 links in
+   registers; GF_SWEEP_PIPELINED stages them through shared memory with asynchronous
+   copies one tile ahead (persistent CTAs).  Both give the same results.  AUTO [default]
+   = PIPELINED for FP32-12; other storages always use the register kernel, and asking
+   them for PIPELINED returns GF_EINVAL. */
+#define GF_SWEEP_AUTO 0
+#define GF_SWEEP_REGISTER 1
+#define GF_SWEEP_PIPELINED 2
+GF_API int gf_set_sweep_variant(gf_handle *h, int variant);
 
 /* Sweeps done by the last gf_fix in the FP32 and FP64 phases (mixed mode), nullable. */
 GF_API int gf_fix_phase_sweeps(const gf_handle *h, int *fp32_sweeps, int *fp64_sweeps);

@@ -22,16 +22,20 @@ namespace gf {
 void launch_sweep_fp64(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_sweep_fp64_repro(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
+cudaError_t prepare_sweep_pipe();
 void launch_measure_fp64(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_measure_fp32(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
                          cudaStream_t s);
 void launch_fill_int(int* p, int value, int n, cudaStream_t s);
 
-void launch_sweep(int storage, int nd, bool repro, const SweepArgs& a, int n_tiles, int threads,
-                  cudaStream_t s) {
+void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs& a, int n_tiles,
+                  int threads, cudaStream_t s) {
   if (storage == GF_FP64_18) {
     if (repro) launch_sweep_fp64_repro(nd, a, n_tiles, threads, s);
     else launch_sweep_fp64(nd, a, n_tiles, threads, s);
+  } else if (storage == GF_FP32_12 && variant != GF_SWEEP_REGISTER) {
+    launch_sweep_fp32_pipe(nd, a, n_tiles, threads, s);
   } else {
     launch_sweep_fp32(storage, nd, a, n_tiles, threads, s);
   }
@@ -178,6 +182,7 @@ struct gf_handle {
   // settings
   double omega = 1.7, eps_switch = 1e-8;
   int form = GF_OR_FIRST_ORDER, reunit_interval = 20, check_interval = 1;
+  int variant = GF_SWEEP_AUTO;
   bool repro = false;
   // state
   int cur = 0;  // 0: primary buffer holds the field, 1: FP64 polish buffer
@@ -248,8 +253,10 @@ int build_tiles(gf_handle* h) {
   return GF_OK;
 }
 
-SweepArgs sweep_args(gf_handle* h, int parity, bool loop) {
+SweepArgs sweep_args(gf_handle* h, int parity, bool loop, int reverse) {
   SweepArgs a{};
+  a.n_tiles = h->n_tiles;
+  a.reverse = reverse;
   a.links = cur_links(h);
   a.lats = cur_lats(h);
   a.tiles = h->d_tiles;
@@ -264,8 +271,10 @@ SweepArgs sweep_args(gf_handle* h, int parity, bool loop) {
   return a;
 }
 
-MeasureArgs measure_args(gf_handle* h, int parity, bool loop) {
+MeasureArgs measure_args(gf_handle* h, int parity, bool loop, int reverse) {
   MeasureArgs a{};
+  a.n_tiles = h->n_tiles;
+  a.reverse = reverse;
   a.links = cur_links(h);
   a.lats = cur_lats(h);
   a.tiles = h->d_tiles;
@@ -304,23 +313,27 @@ FinishArgs finish_args(gf_handle* h, int mode) {
 // F and theta of every unit and lattice, all units (mode MEASURE or RESET), async.
 int enqueue_measure_all(gf_handle* h, int mode) {
   const int st = cur_storage(h);
-  launch_measure(st, h->nd, measure_args(h, 0, false), h->n_tiles, h->threads, h->stream);
+  launch_measure(st, h->nd, measure_args(h, 0, false, 0), h->n_tiles, h->threads, h->stream);
   GF_CK_LAUNCH(h);
-  launch_measure(st, h->nd, measure_args(h, 1, false), h->n_tiles, h->threads, h->stream);
+  launch_measure(st, h->nd, measure_args(h, 1, false, 1), h->n_tiles, h->threads, h->stream);
   GF_CK_LAUNCH(h);
   launch_finish(finish_args(h, mode), h->stream);
   GF_CK_LAUNCH(h);
   return GF_OK;
 }
 
-// One sweep of the device-driven loop (four launches).
-int enqueue_loop_sweep(gf_handle* h, cudaStream_t s) {
+// One sweep of the device-driven loop (four launches).  Consecutive passes over the
+// links walk the tiles in opposite directions, so each pass starts on the lines the
+// previous one left in L2; `pass` counts the passes (3 per sweep).
+int enqueue_loop_sweep(gf_handle* h, cudaStream_t s, int* pass) {
   const int st = cur_storage(h);
-  launch_sweep(st, h->nd, h->repro, sweep_args(h, 0, true), h->n_tiles, h->threads, s);
+  launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 0, true, (*pass)++ & 1), h->n_tiles,
+               h->threads, s);
   GF_CK_LAUNCH(h);
-  launch_sweep(st, h->nd, h->repro, sweep_args(h, 1, true), h->n_tiles, h->threads, s);
+  launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 1, true, (*pass)++ & 1), h->n_tiles,
+               h->threads, s);
   GF_CK_LAUNCH(h);
-  launch_measure(st, h->nd, measure_args(h, 0, true), h->n_tiles, h->threads, s);
+  launch_measure(st, h->nd, measure_args(h, 0, true, (*pass)++ & 1), h->n_tiles, h->threads, s);
   GF_CK_LAUNCH(h);
   launch_finish(finish_args(h, FINISH_LOOP), s);
   GF_CK_LAUNCH(h);
@@ -330,8 +343,8 @@ int enqueue_loop_sweep(gf_handle* h, cudaStream_t s) {
 int ensure_graph(gf_handle* h) {
   if (h->graph[h->cur]) return GF_OK;
   GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = GF_OK;
-  for (int j = 0; j < kGraphSweeps && rc == GF_OK; ++j) rc = enqueue_loop_sweep(h, h->cap_stream);
+  int rc = GF_OK, pass = 0;  // kGraphSweeps * 3 passes: even, so replays keep alternating
+  for (int j = 0; j < kGraphSweeps && rc == GF_OK; ++j) rc = enqueue_loop_sweep(h, h->cap_stream, &pass);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
   if (rc != GF_OK) {
@@ -448,6 +461,10 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(GF_ECUDA, "cudaStreamCreate failed");
+  {
+    cudaError_t e = prepare_sweep_pipe();
+    if (e != cudaSuccess) return bail(GF_ECUDA, std::string("sweep kernel set-up: ") + cudaGetErrorString(e));
+  }
   const Layout& L = h->L;
   char* w = h->ws;
   h->links = w + L.links;
@@ -590,9 +607,9 @@ int gf_or_sweep(gf_handle* h, int parity, double omega) {
   const int st = cur_storage(h);
   for (int p = 0; p < 2; ++p) {
     if (parity != 2 && p != parity) continue;
-    SweepArgs a = sweep_args(h, p, false);
+    SweepArgs a = sweep_args(h, p, false, p);
     a.omega = omega;
-    launch_sweep(st, h->nd, h->repro, a, h->n_tiles, h->threads, h->stream);
+    launch_sweep(st, h->nd, h->repro, h->variant, a, h->n_tiles, h->threads, h->stream);
     GF_CK_LAUNCH(h);
   }
   return GF_OK;
@@ -685,6 +702,17 @@ int gf_set_block_size(gf_handle* h, int threads) {
   if (threads == h->threads) return GF_OK;
   h->threads = threads;
   return build_tiles(h);
+}
+
+int gf_set_sweep_variant(gf_handle* h, int variant) {
+  if (!h) return GF_EINVAL;
+  if (variant != GF_SWEEP_AUTO && variant != GF_SWEEP_REGISTER && variant != GF_SWEEP_PIPELINED)
+    return fail(h, GF_EINVAL, "unknown sweep variant");
+  if (variant == GF_SWEEP_PIPELINED && h->storage != GF_FP32_12)
+    return fail(h, GF_EINVAL, "the pipelined sweep exists for GF_FP32_12 storage only");
+  if (variant != h->variant) drop_graphs(h);
+  h->variant = variant;
+  return GF_OK;
 }
 
 int gf_fix_phase_sweeps(const gf_handle* h, int* fp32_sweeps, int* fp64_sweeps) {

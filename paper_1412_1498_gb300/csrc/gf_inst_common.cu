@@ -3,7 +3,7 @@
 
 namespace gf {
 
-__global__ void __launch_bounds__(256) k_finish(FinishArgs a) {
+__global__ void __launch_bounds__(512) k_finish(FinishArgs a) {
   __shared__ double red[96];
   __shared__ int s_last;
   const int u = blockIdx.x;
@@ -17,12 +17,30 @@ __global__ void __launch_bounds__(256) k_finish(FinishArgs a) {
   const bool reduce = loop ? (was_active && check) : true;
   if (reduce) {
     const int tb = a.unit_tiles[u], te = a.unit_tiles[u + 1];
-    double v[3] = {0.0, 0.0, 0.0};
-    for (int i = tb + (int)threadIdx.x; i < te; i += blockDim.x) {
-      v[0] += a.part_F[i];
-      v[1] += a.part_th_even[i];
-      v[2] += a.part_th_odd[i];
+    // 8 independent accumulators per value so that the loads of a pass are all in
+    // flight together; combined in a fixed order (deterministic)
+    constexpr int U = 8;
+    double acc[3][U];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < U; ++j) acc[k][j] = 0.0;
+    const int stride = (int)blockDim.x;
+    for (int i0 = tb + (int)threadIdx.x; i0 < te; i0 += U * stride) {
+#pragma unroll
+      for (int j = 0; j < U; ++j) {
+        const int i = i0 + j * stride;
+        if (i < te) {
+          acc[0][j] += a.part_F[i];
+          acc[1][j] += a.part_th_even[i];
+          acc[2][j] += a.part_th_odd[i];
+        }
+      }
     }
+    double v[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      v[k] = ((acc[k][0] + acc[k][1]) + (acc[k][2] + acc[k][3])) + ((acc[k][4] + acc[k][5]) + (acc[k][6] + acc[k][7]));
     block_sum<3>(v, red);
     if (threadIdx.x == 0) {
       const LatDev lat = a.lats[a.unit_lat[u]];
@@ -73,7 +91,7 @@ __global__ void __launch_bounds__(256) k_finish(FinishArgs a) {
   }
 }
 
-void launch_finish(const FinishArgs& a, cudaStream_t s) { k_finish<<<a.n_units, 256, 0, s>>>(a); }
+void launch_finish(const FinishArgs& a, cudaStream_t s) { k_finish<<<a.n_units, 512, 0, s>>>(a); }
 
 // ---------------------------------------------------------------------------------
 // element kernels

@@ -1,7 +1,49 @@
 // gf_inst_fp32.cu -- FP32 sweeps (12- and 18-real storage) and FP32 measurement.
 #include "gf_kernels.cuh"
+#include "gf_sweep_pipe.cuh"
 
 namespace gf {
+
+namespace {
+constexpr int kMaxDev = 64;
+int g_pipe_grid[kMaxDev][2][3];  // [device][nd == 4][threads 64/128/256] persistent grid size
+}  // namespace
+
+static int threads_slot(int threads) { return threads == 64 ? 0 : threads == 128 ? 1 : 2; }
+
+// Shared-memory opt-in and persistent grid size for the pipelined sweep (call outside
+// any stream capture, before the first launch on a device).
+cudaError_t prepare_sweep_pipe() {
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= kMaxDev) return cudaErrorInvalidDevice;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  for (int n = 0; n < 2; ++n) {
+    auto kern = n ? k_or_sweep_pipe<4> : k_or_sweep_pipe<3>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * kPipeWords * 256 * sizeof(float4)));
+    if (e != cudaSuccess) return e;
+    for (int t : {64, 128, 256}) {
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, t, 2 * kPipeWords * t * sizeof(float4));
+      if (e != cudaSuccess) return e;
+      g_pipe_grid[dev][n][threads_slot(t)] = per_sm * sms;
+    }
+  }
+  return cudaSuccess;
+}
+
+void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int grid = g_pipe_grid[dev < kMaxDev ? dev : 0][nd == 4][threads_slot(threads)];
+  if (grid <= 0) grid = 1;
+  if (grid > n_tiles) grid = n_tiles;
+  const size_t smem = 2 * kPipeWords * threads * sizeof(float4);
+  if (nd == 4) k_or_sweep_pipe<4><<<grid, threads, smem, s>>>(a);
+  else k_or_sweep_pipe<3><<<grid, threads, smem, s>>>(a);
+}
 
 void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int threads,
                        cudaStream_t s) {

@@ -160,6 +160,8 @@ struct SweepArgs {
   int form;
   int reunit;              // used when st == nullptr
   int measure;             // used when st == nullptr
+  int n_tiles;
+  int reverse;             // walk the tiles last to first (L2 reuse across passes)
   double omega;
 };
 
@@ -172,6 +174,8 @@ struct MeasureArgs {
   double* part_F;          // nullable: per tile sum of Re Tr over the 2 nd links of each site
   double* part_theta;      // per tile sum of Tr[Delta Delta^+]
   int parity;
+  int n_tiles;
+  int reverse;
 };
 
 struct FinishArgs {
@@ -216,7 +220,8 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
     reunit_now = a.parity == 1 && state_reunit_sweep(a.st);
     measure_now = a.parity == 1 && state_check_sweep(a.st);
   }
-  const int4 tile = a.tiles[blockIdx.x];
+  const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
+  const int4 tile = a.tiles[ti];
   if (a.active && !a.active[tile.w]) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   if (measure_now) {
     double v[1] = {q};
     block_sum<1>(v, red);
-    if (threadIdx.x == 0) a.part_theta[blockIdx.x] = v[0];
+    if (threadIdx.x == 0) a.part_theta[ti] = v[0];
   }
 }
 
@@ -312,7 +317,8 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   constexpr int NE = St::NE;
   __shared__ double red[64];
   if (a.st && (!state_running(a.st) || !state_check_sweep(a.st))) return;
-  const int4 tile = a.tiles[blockIdx.x];
+  const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
+  const int4 tile = a.tiles[ti];
   if (a.active && !a.active[tile.w]) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
@@ -327,13 +333,28 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
     T fs = T(0);
+    if constexpr (sizeof(T) == 4) {
+      // FP32: issue all 2 nd link loads before any arithmetic (memory-level parallelism)
+      cx<T> f[ND][NE], b[ND][NE];
 #pragma unroll
-    for (int nu = 0; nu < ND; ++nu) {
-      cx<T> f[NE], b[NE];
-      St::load(base, lat.V, nu, idx_f, f);
-      St::load(base, lat.V, nu, (1 - p) * lat.Vh + (int)(back_lexi(lat, s, nu) >> 1), b);
-      fs = fs + (re_trace(f) + re_trace(b));
-      add_to_A(A, f, b);
+      for (int nu = 0; nu < ND; ++nu) {
+        St::load(base, lat.V, nu, idx_f, f[nu]);
+        St::load(base, lat.V, nu, (1 - p) * lat.Vh + (int)(back_lexi(lat, s, nu) >> 1), b[nu]);
+      }
+#pragma unroll
+      for (int nu = 0; nu < ND; ++nu) {
+        fs = fs + (re_trace(f[nu]) + re_trace(b[nu]));
+        add_to_A(A, f[nu], b[nu]);
+      }
+    } else {
+#pragma unroll
+      for (int nu = 0; nu < ND; ++nu) {
+        cx<T> f[NE], b[NE];
+        St::load(base, lat.V, nu, idx_f, f);
+        St::load(base, lat.V, nu, (1 - p) * lat.Vh + (int)(back_lexi(lat, s, nu) >> 1), b);
+        fs = fs + (re_trace(f) + re_trace(b));
+        add_to_A(A, f, b);
+      }
     }
     fsum = (double)fs;
     q = theta_site(A);
@@ -341,8 +362,8 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   double v[2] = {fsum, q};
   block_sum<2>(v, red);
   if (threadIdx.x == 0) {
-    if (a.part_F) a.part_F[blockIdx.x] = v[0];
-    a.part_theta[blockIdx.x] = v[1];
+    if (a.part_F) a.part_F[ti] = v[0];
+    a.part_theta[ti] = v[1];
   }
 }
 
@@ -351,7 +372,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
 // lattice totals and the loop state.  One block per unit; the last block to finish
 // does the lattice totals (deterministic: fixed summation order everywhere).
 // ----------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_finish(FinishArgs a);
+__global__ void __launch_bounds__(512) k_finish(FinishArgs a);
 
 // ----------------------------------------------------------------------------------
 // Element kernels over all links: layout conversion, reunitarisation, FP32 -> FP64.
@@ -372,8 +393,8 @@ __global__ void k_to_fp64(const char* src, char* dst, LatDev lat_src, LatDev lat
 // ----------------------------------------------------------------------------------
 // Host-side launchers (defined in the instantiation units)
 // ----------------------------------------------------------------------------------
-void launch_sweep(int storage, int nd, bool repro, const SweepArgs& a, int n_tiles, int threads,
-                  cudaStream_t s);
+void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs& a, int n_tiles,
+                  int threads, cudaStream_t s);
 void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_finish(const FinishArgs& a, cudaStream_t s);
 void launch_pack(int storage, char* links, const LatDev& lat, const double* src, long long s0,

@@ -1,0 +1,157 @@
+// gf_sweep_pipe.cuh -- FP32-12 half-sweep with the links staged through shared memory.
+//
+// The register kernel (k_or_sweep) holds a site's 8 links (96 floats) in registers from
+// load to store, which caps it at 8 resident warps per SM and leaves the memory system
+// latency-bound.  Here each thread copies its site's 24 link words (8 links x 3 float4)
+// into shared memory with cp.async, which holds no registers while in flight, one tile
+// ahead of the tile it is computing (double buffer).  The CTAs are persistent: CTA c
+// takes tiles c, c + gridDim, ... so that with tiles walked in reverse the whole grid
+// moves through the lattice as one front.  Every thread reads back only the words it
+// copied itself, so cp.async.wait_group is the only synchronisation the pipeline needs.
+// The arithmetic is the register kernel's, in the same order: both give the same bits.
+#pragma once
+
+#include "gf_kernels.cuh"
+
+namespace gf {
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_but_newest() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+constexpr int kPipeWords = 24;  // fwd mu = 0..3 (3 words each), then bwd mu = 0..3
+
+struct PipeSite {
+  int ti;      // tile index
+  int lat;     // lattice index
+  int idx_f;   // parity-split index of the site
+  int idx_b[4];
+  bool active; // unit active (uniform over the block)
+  bool valid;  // active and inside the tile's slice
+};
+
+// Start the copies of tile k into buffer buf; returns where the site's links live.
+__device__ __forceinline__ PipeSite pipe_issue(const SweepArgs& a, int k, int buf, float4* sm) {
+  PipeSite ps;
+  ps.ti = a.reverse ? a.n_tiles - 1 - k : k;
+  const int4 tile = a.tiles[ps.ti];
+  ps.lat = tile.x;
+  ps.active = a.active == nullptr || a.active[tile.w] != 0;
+  const LatDev lat = a.lats[tile.x];
+  const int h3 = tile.z + (int)threadIdx.x;
+  ps.valid = ps.active && h3 < lat.V3h;
+  if (ps.valid) {
+    const int p = a.parity;
+    const int h = tile.y * lat.V3h + h3;
+    const Site s = site_of(lat, p, h);
+    ps.idx_f = p * lat.Vh + h;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) ps.idx_b[mu] = (1 - p) * lat.Vh + (int)(back_lexi(lat, s, mu) >> 1);
+    const float4* g = reinterpret_cast<const float4*>(a.links + lat.off_bytes);
+    const int B = blockDim.x;
+    float4* slot = sm + (buf * kPipeWords) * B + threadIdx.x;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu)
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        cp_async16(slot + (3 * mu + w) * B, g + (long long)(w * 4 + mu) * lat.V + ps.idx_f);
+        cp_async16(slot + (12 + 3 * mu + w) * B, g + (long long)(w * 4 + mu) * lat.V + ps.idx_b[mu]);
+      }
+  }
+  return ps;
+}
+
+__device__ __forceinline__ void pipe_read(const float4* slot, int B, int word0, cx<float> (&e)[6]) {
+#pragma unroll
+  for (int w = 0; w < 3; ++w) {
+    const float4 v = slot[(word0 + w) * B];
+    e[2 * w] = {v.x, v.y};
+    e[2 * w + 1] = {v.z, v.w};
+  }
+}
+
+template <int ND>
+__global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
+  extern __shared__ float4 sm[];
+  __shared__ double red[32];
+  bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
+  if (a.st) {
+    if (!state_running(a.st)) return;
+    reunit_now = a.parity == 1 && state_reunit_sweep(a.st);
+    measure_now = a.parity == 1 && state_check_sweep(a.st);
+  }
+  int k = blockIdx.x;
+  if (k >= a.n_tiles) return;
+  const int B = blockDim.x;
+  const float omega = (float)a.omega;
+  int buf = 0;
+  PipeSite cur = pipe_issue(a, k, 0, sm);
+  cp_async_commit();
+  for (;;) {
+    const int kn = k + (int)gridDim.x;
+    PipeSite nxt;
+    if (kn < a.n_tiles) nxt = pipe_issue(a, kn, buf ^ 1, sm);
+    cp_async_commit();
+    cp_async_wait_all_but_newest();  // this thread's copies of tile k have landed
+    if (cur.active) {
+      double q = 0.0;
+      if (cur.valid) {
+        const LatDev lat = a.lats[cur.lat];
+        float4* g = reinterpret_cast<float4*>(a.links + lat.off_bytes);
+        const float4* slot = sm + (buf * kPipeWords) * B + threadIdx.x;
+        cx<float> K[9], G[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) K[e] = {0.f, 0.f};
+#pragma unroll
+        for (int mu = 0; mu < ND; ++mu) {
+          cx<float> f[6], b[6];
+          pipe_read(slot, B, 3 * mu, f);
+          pipe_read(slot, B, 12 + 3 * mu, b);
+          add_to_K(K, f, b);
+        }
+        su3_update<float, false>(K, G, omega, a.form);
+        cx<float> A[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) A[e] = {0.f, 0.f};
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+          cx<float> f[6], b[6];
+          pipe_read(slot, B, 3 * mu, f);
+          pipe_read(slot, B, 12 + 3 * mu, b);
+          left_mul(G, f);
+          right_mul_dag(b, G);
+          if (reunit_now) {
+            reunit(f);
+            reunit(b);
+          }
+          if (mu < ND && measure_now) add_to_A(A, f, b);
+#pragma unroll
+          for (int w = 0; w < 3; ++w) {
+            g[(long long)(w * 4 + mu) * lat.V + cur.idx_f] =
+                make_float4(f[2 * w].re, f[2 * w].im, f[2 * w + 1].re, f[2 * w + 1].im);
+            g[(long long)(w * 4 + mu) * lat.V + cur.idx_b[mu]] =
+                make_float4(b[2 * w].re, b[2 * w].im, b[2 * w + 1].re, b[2 * w + 1].im);
+          }
+        }
+        if (measure_now) q = theta_site(A);
+      }
+      if (measure_now) {
+        double v[1] = {q};
+        block_sum<1>(v, red);
+        if (threadIdx.x == 0) a.part_theta[cur.ti] = v[0];
+        __syncthreads();  // red[] is reused by the next tile
+      }
+    }
+    if (kn >= a.n_tiles) break;
+    k = kn;
+    buf ^= 1;
+    cur = nxt;
+  }
+}
+
+}  // namespace gf

@@ -267,3 +267,25 @@ def test_block_sizes_agree(gf, threads):
         outs.append((fx.download(), o["F"][0]))
         fx.close()
     assert np.array_equal(outs[0][0], outs[1][0])
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+@pytest.mark.parametrize("threads", [64, 128, 256])
+def test_pipelined_sweep_equals_register_sweep(gf, gauge, threads):
+    # the shared-memory pipelined FP32-12 kernel does the register kernel's arithmetic
+    # in the same order: same bits, with reunitarisation, checks and Coulomb masks
+    dims = DIMS if gauge == 0 else DIMS_C
+    U = fields.random_gauge_config(dims, 0.5, 72)
+    outs = []
+    for variant in (gf.GF_SWEEP_REGISTER, gf.GF_SWEEP_PIPELINED):
+        fx = make(gf, dims, gauge, gf.GF_FP32_12)
+        gf.gf_set_sweep_variant(fx.h, variant)
+        gf.gf_set_block_size(fx.h, threads)
+        fx.upload(U)
+        o1 = fx.fix(1e-300, 30)
+        o2 = fx.fix(1e-6, 300)
+        outs.append((fx.download(), o1["F"][0], o1["theta"][0], o2["iters"].copy(), o2["theta"][0]))
+        fx.close()
+    a, b = outs
+    assert np.array_equal(a[0], b[0])
+    assert a[1:3] == b[1:3] and np.array_equal(a[3], b[3]) and a[4] == b[4]
