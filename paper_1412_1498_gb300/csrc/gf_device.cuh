@@ -328,4 +328,63 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* smem /* NV * 
   }
 }
 
+// ----------------------------------------------------------------------------------
+// Block reduction of FP32 values without FP64 arithmetic per thread (FP64 issues at a
+// small fraction of the FP32 rate on this GPU): a compensated (TwoSum, Knuth) tree in
+// FP32 keeps each partial as an unevaluated sum hi + lo, so the block total is exact to
+// about 2^-44 relative; one conversion to FP64 per block.  Fixed order: deterministic.
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], double (&out)[NV],
+                                              float* smem /* 2 * NV * 32 */) {
+  float hi[NV], lo[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    hi[k] = v[k];
+    lo[k] = 0.f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const float oh = __shfl_down_sync(0xffffffffu, hi[k], o);
+      const float ol = __shfl_down_sync(0xffffffffu, lo[k], o);
+      float s, e;
+      two_sum(hi[k], oh, s, e);
+      hi[k] = s;
+      lo[k] = (lo[k] + ol) + e;
+    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      smem[(2 * k) * 32 + warp] = hi[k];
+      smem[(2 * k + 1) * 32 + warp] = lo[k];
+    }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float h = lane < nw ? smem[(2 * k) * 32 + lane] : 0.f;
+      float l = lane < nw ? smem[(2 * k + 1) * 32 + lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, h, o);
+        const float ol = __shfl_down_sync(0xffffffffu, l, o);
+        float s, e;
+        two_sum(h, oh, s, e);
+        h = s;
+        l = (l + ol) + e;
+      }
+      out[k] = (double)h + (double)l;
+    }
+  }
+}
+
 }  // namespace gf

@@ -129,7 +129,7 @@ __device__ __forceinline__ void add_to_A(cx<T> (&A)[9], const cx<T> (&f)[NE], co
 
 // Tr[Delta Delta^dagger] with Delta = A - A^dagger - (1/3) Tr(A - A^dagger)
 template <class T>
-__device__ __forceinline__ double theta_site(const cx<T> (&A)[9]) {
+__device__ __forceinline__ T theta_site(const cx<T> (&A)[9]) {
   cx<T> D[9];
 #pragma unroll
   for (int i = 0; i < 3; ++i)
@@ -143,7 +143,23 @@ __device__ __forceinline__ double theta_site(const cx<T> (&A)[9]) {
   T q = T(0);
 #pragma unroll
   for (int e = 0; e < 9; ++e) q = q + (D[e].re * D[e].re + D[e].im * D[e].im);
-  return (double)q;
+  return q;
+}
+
+// Per-tile partial sums: FP64 storage reduces in FP64; FP32 storage in compensated FP32
+// with one conversion per block (see block_sum_f32).
+template <class T, int NV>
+__device__ __forceinline__ void tile_sum(const T (&v)[NV], double (&out)[NV], double* smem64) {
+  if constexpr (sizeof(T) == 8) {
+    double w[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w[k] = v[k];
+    block_sum<NV>(w, smem64);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = w[k];
+  } else {
+    block_sum_f32<NV>(v, out, reinterpret_cast<float*>(smem64));
+  }
 }
 
 // ----------------------------------------------------------------------------------
@@ -225,7 +241,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   if (a.active && !a.active[tile.w]) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
-  double q = 0.0;
+  T q = T(0);
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
@@ -299,9 +315,10 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
     }
   }
   if (measure_now) {
-    double v[1] = {q};
-    block_sum<1>(v, red);
-    if (threadIdx.x == 0) a.part_theta[ti] = v[0];
+    const T v[1] = {q};
+    double o[1];
+    tile_sum<T, 1>(v, o, red);
+    if (threadIdx.x == 0) a.part_theta[ti] = o[0];
   }
 }
 
@@ -322,7 +339,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   if (a.active && !a.active[tile.w]) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
-  double fsum = 0.0, q = 0.0;
+  T fsum = T(0), q = T(0);
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
@@ -356,14 +373,15 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
         add_to_A(A, f, b);
       }
     }
-    fsum = (double)fs;
+    fsum = fs;
     q = theta_site(A);
   }
-  double v[2] = {fsum, q};
-  block_sum<2>(v, red);
+  const T v[2] = {fsum, q};
+  double o[2];
+  tile_sum<T, 2>(v, o, red);
   if (threadIdx.x == 0) {
-    if (a.part_F) a.part_F[ti] = v[0];
-    a.part_theta[ti] = v[1];
+    if (a.part_F) a.part_F[ti] = o[0];
+    a.part_theta[ti] = o[1];
   }
 }
 

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
     cp_async_commit();
     cp_async_wait_all_but_newest();  // this thread's copies of tile k have landed
     if (cur.active) {
-      double q = 0.0;
+      float q = 0.f;
       if (cur.valid) {
         const LatDev lat = a.lats[cur.lat];
         float4* g = reinterpret_cast<float4*>(a.links + lat.off_bytes);
@@ -141,9 +141,10 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
         if (measure_now) q = theta_site(A);
       }
       if (measure_now) {
-        double v[1] = {q};
-        block_sum<1>(v, red);
-        if (threadIdx.x == 0) a.part_theta[cur.ti] = v[0];
+        const float v[1] = {q};
+        double o[1];
+        block_sum_f32<1>(v, o, reinterpret_cast<float*>(red));
+        if (threadIdx.x == 0) a.part_theta[cur.ti] = o[0];
         __syncthreads();  // red[] is reused by the next tile
       }
     }
