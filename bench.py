@@ -269,8 +269,11 @@ def run_gpu(args):
     ttt = None
     if not args.skip_time_to_theta:
         ttt = {}
-        for name, storage, mixed in (("mixed", gf.GF_FP32_12, True), ("fp64", gf.GF_FP64_18, False)):
+        for name, storage, mixed, polish in (("mixed", gf.GF_FP32_12, True, gf.GF_POLISH_FP64),
+                                             ("mixed_split", gf.GF_FP32_12, True, gf.GF_POLISH_SPLIT),
+                                             ("fp64", gf.GF_FP64_18, False, gf.GF_POLISH_FP64)):
             f2 = gf.GaugeFixer(DIMS, gf.GF_LANDAU, storage, mixed=mixed, device=dev)
+            gf.gf_set_polish(f2.h, polish)
             f2.upload(U)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -282,9 +285,9 @@ def run_gpu(args):
             f2.close()
             del f2
             torch.cuda.empty_cache()
-        ttt["F_err_mixed_vs_fp64"] = abs(ttt["mixed"]["F"] - ttt["fp64"]["F"])
-        ttt["theta_mixed"] = ttt["mixed"]["theta"]
-        ttt["speedup_mixed_over_fp64"] = ttt["fp64"]["seconds"] / ttt["mixed"]["seconds"]
+        for m in ("mixed", "mixed_split"):
+            ttt[f"F_err_{m}_vs_fp64"] = abs(ttt[m]["F"] - ttt["fp64"]["F"])
+            ttt[f"speedup_{m}_over_fp64"] = ttt["fp64"]["seconds"] / ttt[m]["seconds"]
 
     peak, peak_kind = measured_peaks()
     achieved = HALF_SWEEP_BYTES / (half_ms * 1e-3) / 1e9

@@ -190,6 +190,17 @@ GF_API int gf_set_block_size(gf_handle *h, int threads);      /* [128]; 64, 128 
    copies one tile ahead (persistent CTAs).  Both give the same results.  AUTO [default]
    = PIPELINED for FP32-12; other storages always use the register kernel, and asking
    them for PIPELINED returns GF_EINVAL. */
+/* Arithmetic of the polish phase of a mixed-precision gf_fix (GF_FLAG_MIXED):
+   GF_POLISH_FP64 [default]: FP64-18 sweeps.
+   GF_POLISH_SPLIT: double-float sweeps (each real an unevaluated sum of two floats, about
+   48-bit precision, no FP64 arithmetic in the sweep) with the first-order
+   overrelaxation form, then conversion to FP64-18 with an FP64 reunitarisation and
+   FP64 sweeps until theta, measured in FP64, is below eps.  With GF_OR_EXACT the FP64
+   polish is used. */
+#define GF_POLISH_FP64 0
+#define GF_POLISH_SPLIT 1
+GF_API int gf_set_polish(gf_handle *h, int polish);
+
 #define GF_SWEEP_AUTO 0
 #define GF_SWEEP_REGISTER 1
 #define GF_SWEEP_PIPELINED 2

@@ -28,6 +28,7 @@ UNITS = {
     "gf_inst_fp64_repro.cu": ["-fmad=false"],
     "gf_inst_fp32.cu": [],
     "gf_noalloc.cu": [],
+    "gf_inst_split.cu": [],
 }
 
 

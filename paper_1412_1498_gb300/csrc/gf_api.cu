@@ -24,6 +24,14 @@ void launch_sweep_fp64_repro(int nd, const SweepArgs& a, int n_tiles, int thread
 void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 cudaError_t prepare_sweep_pipe();
+void launch_sweep_split(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_measure_split(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_to_split(int storage, const char* src, char* dst, const LatDev& ls, const LatDev& ld,
+                     cudaStream_t s);
+void launch_split_to_fp64(char* links, const LatDev& lat, cudaStream_t s);
+
+// internal storage code of the double-float polish copy (never visible in the C ABI)
+constexpr int kSplit18 = 100;
 void launch_measure_fp64(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_measure_fp32(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
                          cudaStream_t s);
@@ -31,7 +39,9 @@ void launch_fill_int(int* p, int value, int n, cudaStream_t s);
 
 void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs& a, int n_tiles,
                   int threads, cudaStream_t s) {
-  if (storage == GF_FP64_18) {
+  if (storage == kSplit18) {
+    launch_sweep_split(nd, a, n_tiles, threads, s);
+  } else if (storage == GF_FP64_18) {
     if (repro) launch_sweep_fp64_repro(nd, a, n_tiles, threads, s);
     else launch_sweep_fp64(nd, a, n_tiles, threads, s);
   } else if (storage == GF_FP32_12 && variant != GF_SWEEP_REGISTER) {
@@ -43,7 +53,8 @@ void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs&
 
 void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
                     cudaStream_t s) {
-  if (storage == GF_FP64_18) launch_measure_fp64(nd, a, n_tiles, threads, s);
+  if (storage == kSplit18) launch_measure_split(nd, a, n_tiles, threads, s);
+  else if (storage == GF_FP64_18) launch_measure_fp64(nd, a, n_tiles, threads, s);
   else launch_measure_fp32(storage, nd, a, n_tiles, threads, s);
 }
 }  // namespace gf
@@ -183,12 +194,14 @@ struct gf_handle {
   double omega = 1.7, eps_switch = 1e-8;
   int form = GF_OR_FIRST_ORDER, reunit_interval = 20, check_interval = 1;
   int variant = GF_SWEEP_AUTO;
+  int polish = GF_POLISH_FP64;
   bool repro = false;
   // state
-  int cur = 0;  // 0: primary buffer holds the field, 1: FP64 polish buffer
+  int cur = 0;  // 0: primary buffer holds the field, 1: polish buffer in FP64-18,
+                // 2: polish buffer in double-float (only inside gf_fix)
   int phase_sweeps[2] = {0, 0};
-  // graphs: one per buffer
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  // graphs: one per buffer state
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
   std::string err;
 };
 
@@ -216,10 +229,12 @@ void drop_graphs(gf_handle* h) {
     }
 }
 
-int cur_storage(const gf_handle* h) { return h->cur == 1 ? GF_FP64_18 : h->storage; }
-char* cur_links(const gf_handle* h) { return h->cur == 1 ? h->links64 : h->links; }
-LatDev* cur_lats(const gf_handle* h) { return h->cur == 1 ? h->d_lats64 : h->d_lats; }
-const LatDev& cur_lat_host(const gf_handle* h, int l) { return h->cur == 1 ? h->lats64[l] : h->lats[l]; }
+int cur_storage(const gf_handle* h) {
+  return h->cur == 2 ? kSplit18 : h->cur == 1 ? GF_FP64_18 : h->storage;
+}
+char* cur_links(const gf_handle* h) { return h->cur >= 1 ? h->links64 : h->links; }
+LatDev* cur_lats(const gf_handle* h) { return h->cur >= 1 ? h->d_lats64 : h->d_lats; }
+const LatDev& cur_lat_host(const gf_handle* h, int l) { return h->cur >= 1 ? h->lats64[l] : h->lats[l]; }
 
 // Build the tile table for the current block size and upload it.
 int build_tiles(gf_handle* h) {
@@ -634,14 +649,32 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
   if (mixed) {
     if ((rc = run_phase(h, std::max(eps, h->eps_switch), maxiter, &done)) != GF_OK) return rc;
     h->phase_sweeps[0] = done;
-    for (int l = 0; l < h->n_lat; ++l) {
-      launch_to_fp64(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
-      GF_CK_LAUNCH(h);
-    }
-    h->cur = 1;
     int done2 = 0;
-    if ((rc = run_phase(h, eps, maxiter - done, &done2)) != GF_OK) return rc;
-    h->phase_sweeps[1] = done2;
+    if (h->polish == GF_POLISH_SPLIT && h->form == GF_OR_FIRST_ORDER) {
+      // double-float polish, then FP64 (conversion with an FP64 reunitarisation)
+      for (int l = 0; l < h->n_lat; ++l) {
+        launch_to_split(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
+        GF_CK_LAUNCH(h);
+      }
+      h->cur = 2;
+      rc = run_phase(h, eps, maxiter - done, &done2);
+      for (int l = 0; l < h->n_lat; ++l) {
+        launch_split_to_fp64(h->links64, h->lats64[l], h->stream);
+        GF_CK_LAUNCH(h);
+      }
+      h->cur = 1;
+      if (rc != GF_OK) return rc;
+      done += done2;
+    } else {
+      for (int l = 0; l < h->n_lat; ++l) {
+        launch_to_fp64(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
+        GF_CK_LAUNCH(h);
+      }
+      h->cur = 1;
+    }
+    int done3 = 0;
+    if ((rc = run_phase(h, eps, maxiter - done, &done3)) != GF_OK) return rc;
+    h->phase_sweeps[1] = done2 + done3;
   } else {
     if ((rc = run_phase(h, eps, maxiter, &done)) != GF_OK) return rc;
     h->phase_sweeps[h->cur == 1 || h->storage == GF_FP64_18 ? 1 : 0] = done;
@@ -702,6 +735,13 @@ int gf_set_block_size(gf_handle* h, int threads) {
   if (threads == h->threads) return GF_OK;
   h->threads = threads;
   return build_tiles(h);
+}
+
+int gf_set_polish(gf_handle* h, int polish) {
+  if (!h) return GF_EINVAL;
+  if (polish != GF_POLISH_FP64 && polish != GF_POLISH_SPLIT) return fail(h, GF_EINVAL, "unknown polish mode");
+  h->polish = polish;
+  return GF_OK;
 }
 
 int gf_set_sweep_variant(gf_handle* h, int variant) {

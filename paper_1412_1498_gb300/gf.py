@@ -35,6 +35,7 @@ GF_FP64_18, GF_FP32_18, GF_FP32_12 = 0, 1, 2
 GF_FLAG_MIXED = 1
 GF_OR_FIRST_ORDER, GF_OR_EXACT = 0, 1
 GF_SWEEP_AUTO, GF_SWEEP_REGISTER, GF_SWEEP_PIPELINED = 0, 1, 2
+GF_POLISH_FP64, GF_POLISH_SPLIT = 0, 1
 
 _vp, _int, _dbl, _sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
 _IP, _DP = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)
@@ -62,6 +63,7 @@ _SIGS = {
     "gf_set_block_size": (_int, [_vp, _int]),
     "gf_fix_phase_sweeps": (_int, [_vp, _IP, _IP]),
     "gf_set_sweep_variant": (_int, [_vp, _int]),
+    "gf_set_polish": (_int, [_vp, _int]),
     "gf_functional_theta_noalloc": (_int, [_IP, _int, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -196,6 +198,10 @@ def gf_set_reproducible(h, on: bool) -> None:
 
 def gf_set_block_size(h, threads: int) -> None:
     _check(_lib.gf_set_block_size(h, threads), h)
+
+
+def gf_set_polish(h, polish: int) -> None:
+    _check(_lib.gf_set_polish(h, polish), h)
 
 
 def gf_set_sweep_variant(h, variant: int) -> None:

@@ -289,3 +289,72 @@ def test_pipelined_sweep_equals_register_sweep(gf, gauge, threads):
     a, b = outs
     assert np.array_equal(a[0], b[0])
     assert a[1:3] == b[1:3] and np.array_equal(a[3], b[3]) and a[4] == b[4]
+
+
+# ---------------------------------------------------------------- double-float polish
+def _mixed(gf, dims, gauge, polish, U, eps, maxiter, eps_sw=None):
+    fx = make(gf, dims, gauge, gf.GF_FP32_12, mixed=True)
+    gf.gf_set_polish(fx.h, polish)
+    if eps_sw is not None:
+        gf.gf_set_mixed_switch(fx.h, eps_sw)
+    fx.upload(U)
+    out = fx.fix(eps, maxiter)
+    got = fx.download()
+    fx.close()
+    return out, got
+
+
+def test_split_polish_reaches_1e15_same_maximum(gf):
+    dims = (8, 8, 8, 8)
+    U = fields.random_gauge_config(dims, 0.4, 1, 2)
+    o_s, g_s = _mixed(gf, dims, gf.GF_LANDAU, gf.GF_POLISH_SPLIT, U, 1e-15, 3000)
+    o_d, g_d = _mixed(gf, dims, gf.GF_LANDAU, gf.GF_POLISH_FP64, U, 1e-15, 3000)
+    assert o_s["rc"] == gf.GF_OK and o_d["rc"] == gf.GF_OK
+    # same FP32 phase, then two polishes converging to the same maximum
+    assert o_s["phase_sweeps"][0] == o_d["phase_sweeps"][0]
+    F, th, _, _ = oracle.measure(g_s)
+    assert th < 1e-15 * (1 + 1e-6)
+    assert abs(o_s["theta"][0] - th) <= 1e-9 * th
+    from tests import obs
+    assert obs.unitarity_error(g_s) < 1e-14 and obs.det_error(g_s) < 1e-14
+    assert abs(F - oracle.measure(g_d)[0]) < 1e-11
+    assert np.abs(g_s - g_d).max() < 1e-6
+    # the polish needs as many sweeps as the FP64 one, within a few
+    assert abs(o_s["phase_sweeps"][1] - o_d["phase_sweeps"][1]) <= 0.05 * o_d["phase_sweeps"][1] + 5
+
+
+def test_split_sweeps_track_fp64_near_convergence(gf):
+    # start near the maximum (theta ~ 1e-8): split sweeps against the FP64 oracle's
+    dims = (8, 8, 8, 8)
+    U = fields.random_gauge_config(dims, 0.4, 1, 2)
+    oracle.fix(U, 1e-8, 1000, 1.7)
+    fx = make(gf, dims, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True)
+    gf.gf_set_polish(fx.h, gf.GF_POLISH_SPLIT)
+    gf.gf_set_mixed_switch(fx.h, 1e9)          # no FP32 sweeps: straight to the polish
+    fx.upload(U)
+    fx.fix(1e-300, 0)                          # conversion only (FP32 -> split -> FP64)
+    start = fx.download()
+    fx.close()
+    fx = make(gf, dims, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True)
+    gf.gf_set_polish(fx.h, gf.GF_POLISH_SPLIT)
+    gf.gf_set_mixed_switch(fx.h, 1e9)
+    gf.gf_set_reunit_interval(fx.h, 20)
+    fx.upload(U)
+    out = fx.fix(1e-300, 50)
+    got = fx.download()
+    ref = start.copy()
+    r = oracle.fix(ref, 1e-300, 50, 1.7)
+    err = np.abs(got - ref).max()
+    assert err < 1e-10, err
+    assert abs(out["theta"][0] - r["theta"]) < 1e-6 * r["theta"]
+    fx.close()
+
+
+def test_split_polish_coulomb_per_slice(gf):
+    dims = (6, 4, 6, 8)
+    U = fields.random_gauge_config(dims, 0.5, 73)
+    out, got = _mixed(gf, dims, gf.GF_COULOMB, gf.GF_POLISH_SPLIT, U, 1e-15, 4000)
+    assert out["rc"] == gf.GF_OK
+    F, th, F_t, th_t = oracle.measure(got, oracle.COULOMB)
+    assert np.all(th_t < 1e-15 * (1 + 1e-6)), th_t
+    assert len(set(out["iters"].tolist())) > 1
