@@ -289,6 +289,25 @@ def run_gpu(args):
             ttt[f"F_err_{m}_vs_fp64"] = abs(ttt[m]["F"] - ttt["fp64"]["F"])
             ttt[f"speedup_{m}_over_fp64"] = ttt["fp64"]["seconds"] / ttt[m]["seconds"]
 
+    # ---- double-float polish sweeps on the same field (the polish phase's kernel)
+    split_probe = None
+    if args.split_probe > 0:
+        f3 = gf.GaugeFixer(DIMS, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True, device=dev)
+        gf.gf_set_polish(f3.h, gf.GF_POLISH_SPLIT)
+        gf.gf_set_mixed_switch(f3.h, 1e9)        # no FP32 sweeps: straight to the polish
+        f3.upload(U)
+        gf.gf_fix(f3.h, 1e-300, 2)               # warm-up (graph capture)
+        f3.upload(U)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        gf.gf_fix(f3.h, 1e-300, args.split_probe)
+        p1.record(stream)
+        p1.synchronize()
+        split_probe = {"sweeps": args.split_probe, "ms_per_sweep_incl_conversions": p0.elapsed_time(p1) / args.split_probe,
+                       "link_bytes_per_sweep": 20 * V * 144}
+        f3.close()
+        del f3
+
     peak, peak_kind = measured_peaks()
     achieved = HALF_SWEEP_BYTES / (half_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -323,6 +342,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clocks.summary(),
             "time_to_theta_1e-15": ttt,
+            "split_polish_probe": split_probe,
         }
         print(json.dumps(line))
     fx.close()
@@ -340,6 +360,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--skip-time-to-theta", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--split-probe", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gf":
         args.warmup = 3

@@ -70,6 +70,11 @@ extern "C" {
 /* creation flags */
 #define GF_FLAG_MIXED 1 /* keep an FP64-18 copy: gf_fix runs the FP32 storage down to the
                            switch threshold, converts, then polishes in FP64 */
+#define GF_FLAG_AUTOGRAD 4 /* add the buffers of gf_ad_functional / gf_ad_backward (one
+                              lattice, GF_FP64_18) */
+#define GF_FLAG_FASD 2  /* add the buffers of Fourier-accelerated steepest descent (one
+                           lattice; GF_FP32_12 or GF_FP64_18; power-of-two extents <= 64 in
+                           the transformed directions: x, y, z, and t for Landau gauge) */
 
 /* form of the overrelaxation g -> g^omega per SU(2) subgroup (Section 1, after Eq. (6)) */
 #define GF_OR_FIRST_ORDER 0 /* a' = 1 - omega + omega a, b' = omega b, renormalised */
@@ -173,6 +178,42 @@ GF_API int gf_reunitarize(gf_handle *h);
  *   Synchronises the stream.
  */
 GF_API int gf_fix(gf_handle *h, double eps, int maxiter, int *iters, double *F, double *theta);
+
+/*
+ * Fourier-accelerated steepest descent, Algorithm 2 with Eqs. (7)-(9): one iteration
+ *   Delta(x) (Eq. (3), the argument of Eq. (8)); FFT of each element over the gauge
+ *   directions (4D Landau, 3D per time slice Coulomb); multiply by
+ *   (alpha/2) p^2_max / p^2, p^2 = sum_mu 4 sin^2(pi k_mu / L_mu), p^2_max = 4 nd, the
+ *   k = 0 mode set to 0; inverse FFT and 1/N; g(x) = reunit(1 + Delta~(x)) (first-order
+ *   exponential); U_mu(x) <- g(x) U_mu(x) g(x+mu)^+ for every mu.
+ * Needs a handle created with GF_FLAG_FASD.  Asynchronous.  alpha > 0 (0.08 in the paper,
+ * Sec. 1).  gf_fix runs Algorithm 2 instead of Algorithm 1 after
+ * gf_set_method(h, GF_METHOD_FASD), with gf_set_alpha's alpha [0.08] and the links
+ * reunitarised every reunit_interval iterations; in Coulomb gauge each time slice has
+ * its own stop rule.  Mixed precision does not apply to it.
+ */
+#define GF_METHOD_OR 0
+#define GF_METHOD_FASD 1
+GF_API int gf_fa_sd_step(gf_handle *h, double alpha);
+GF_API int gf_set_method(gf_handle *h, int method);
+GF_API int gf_set_alpha(gf_handle *h, double alpha);
+
+/*
+ * F and theta as differentiable functions of the gauge transformation's Lie-algebra
+ * parameters (the gradient direction of steepest descent, Eq. (7)):
+ *   g(x) = exp(i sum_a c_a(x) lambda_a) (Gell-Mann lambda_a), U^g_mu(x) = g(x) U_mu(x)
+ *   g(x+mu)^+ applied to the handle's current field, F(c) by Eq. (1) and theta(c) by
+ *   Eqs. (2)-(3) of U^g.
+ * gf_ad_functional: c = device array of V x 8 doubles in canonical site order; out =
+ *   device array of 2 doubles, receives (F, theta).
+ * gf_ad_backward: upstream = device (dL/dF, dL/dtheta); grad = device V x 8 doubles,
+ *   overwritten with dL/dc.  g, the transformed links and Delta are recomputed from c
+ *   (nothing is kept from the forward call).  dF/dc_a(x) at c = 0 is
+ *   Tr[lambda_a Delta(x)] / (2i nd Nc V).
+ * Both asynchronous on the handle's stream; the handle needs GF_FLAG_AUTOGRAD.
+ */
+GF_API int gf_ad_functional(gf_handle *h, const double *c, double *out);
+GF_API int gf_ad_backward(gf_handle *h, const double *c, const double *upstream, double *grad);
 
 /* Settings (defaults in brackets).  Each returns GF_EINVAL for an out-of-range value. */
 GF_API int gf_set_omega(gf_handle *h, double omega);          /* [1.7], 1 <= omega < 2       */

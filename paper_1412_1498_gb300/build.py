@@ -29,6 +29,8 @@ UNITS = {
     "gf_inst_fp32.cu": [],
     "gf_noalloc.cu": [],
     "gf_inst_split.cu": [],
+    "gf_inst_fasd.cu": [],
+    "gf_inst_autograd.cu": [],
 }
 
 

@@ -32,6 +32,17 @@ void launch_split_to_fp64(char* links, const LatDev& lat, cudaStream_t s);
 
 // internal storage code of the double-float polish copy (never visible in the C ABI)
 constexpr int kSplit18 = 100;
+
+cudaError_t prepare_fasd(int storage, int nd, const LatDev& lat);
+void launch_fasd_delta_xy(int storage, int nd, const FasdArgs& a, cudaStream_t s);
+void launch_fasd_finish(const FasdArgs& a, cudaStream_t s);
+void launch_fasd_zt(int storage, int nd, const FasdArgs& a, cudaStream_t s);
+void launch_fasd_xy_inv_g(int storage, int nd, const FasdArgs& a, cudaStream_t s);
+void launch_fasd_update(int storage, int nd, const FasdArgs& a, cudaStream_t s);
+void launch_fasd_bump(const FasdArgs& a, cudaStream_t s);
+size_t ad_partial_doubles(long long V);
+void launch_ad_forward(const AdArgs& a, cudaStream_t s);
+void launch_ad_backward(const AdArgs& a, cudaStream_t s);
 void launch_measure_fp64(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_measure_fp32(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
                          cudaStream_t s);
@@ -84,7 +95,8 @@ int link_bytes(int storage) {
 
 struct Layout {
   size_t links, links64, staging, lats, lats64, tiles, unit_tiles, unit_lat, active, iters, partF,
-      pthe, ptho, usF, usT, uF, uT, lF, lT, state, total;
+      pthe, ptho, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT, unit_planes, ad_g,
+      ad_delta, ad_part, ad_ticket, total;
   size_t staging_bytes;
   int max_tiles, n_units;
 };
@@ -143,6 +155,27 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->lF = take(sizeof(double) * n_lat);
   L->lT = take(sizeof(double) * n_lat);
   L->state = take(sizeof(DevState));
+  if (flags & GF_FLAG_FASD) {
+    const int* d = dims;  // one lattice
+    const size_t c = storage == GF_FP64_18 ? 16 : 8;
+    const long long V = (long long)d[0] * d[1] * d[2] * d[3];
+    L->kbuf = take(4 * (size_t)V * c);
+    L->gbuf = take(6 * (size_t)V * c);
+    L->planeF = take(sizeof(double) * d[2] * d[3]);
+    L->planeT = take(sizeof(double) * d[2] * d[3]);
+    L->unit_planes = take(sizeof(int) * (n_units + 1));
+  } else {
+    L->kbuf = L->gbuf = L->planeF = L->planeT = L->unit_planes = (size_t)-1;
+  }
+  if (flags & GF_FLAG_AUTOGRAD) {
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    L->ad_g = take(9 * 16 * (size_t)V);
+    L->ad_delta = take(9 * 16 * (size_t)V);
+    L->ad_part = take(sizeof(double) * ad_partial_doubles(V));
+    L->ad_ticket = take(sizeof(unsigned int));
+  } else {
+    L->ad_g = L->ad_delta = L->ad_part = L->ad_ticket = (size_t)-1;
+  }
   L->total = off;
   L->max_tiles = max_tiles;
   L->n_units = n_units;
@@ -156,7 +189,28 @@ int check_common(int n_lat, const int* dims, int gauge, int storage, int flags, 
     *why = "storage must be GF_FP64_18, GF_FP32_18 or GF_FP32_12";
     return GF_EINVAL;
   }
-  if (flags & ~GF_FLAG_MIXED) { *why = "unknown flag"; return GF_EINVAL; }
+  if (flags & ~(GF_FLAG_MIXED | GF_FLAG_FASD | GF_FLAG_AUTOGRAD)) { *why = "unknown flag"; return GF_EINVAL; }
+  if ((flags & GF_FLAG_AUTOGRAD) && (n_lat != 1 || storage != GF_FP64_18)) {
+    *why = "the differentiable functional takes one lattice in GF_FP64_18 storage";
+    return GF_EINVAL;
+  }
+  if (flags & GF_FLAG_FASD) {
+    if (n_lat != 1) { *why = "Fourier-accelerated steepest descent takes one lattice per handle"; return GF_EINVAL; }
+    if (storage == GF_FP32_18) { *why = "Fourier acceleration supports GF_FP32_12 and GF_FP64_18 storage"; return GF_EINVAL; }
+    const int nfft = gauge == GF_LANDAU ? 4 : 3;
+    for (int k = 0; k < nfft; ++k) {
+      const int L = dims[k];
+      if (L > 64 || (L & (L - 1)) != 0) {
+        *why = "Fourier acceleration needs power-of-two extents <= 64 in the transformed directions";
+        return GF_EINVAL;
+      }
+    }
+    const size_t c = storage == GF_FP64_18 ? 16 : 8;
+    if (4 * (size_t)dims[0] * dims[1] * c > 200 * 1024) {
+      *why = "Lx * Ly too large for the shared-memory plane FFT";
+      return GF_EINVAL;
+    }
+  }
   for (int l = 0; l < n_lat; ++l)
     if (!valid_dims(dims + 4 * l)) {
       char buf[160];
@@ -195,13 +249,23 @@ struct gf_handle {
   int form = GF_OR_FIRST_ORDER, reunit_interval = 20, check_interval = 1;
   int variant = GF_SWEEP_AUTO;
   int polish = GF_POLISH_FP64;
+  int method = GF_METHOD_OR;
+  double alpha = 0.08;
+  void* kbuf = nullptr;
+  char* gbuf = nullptr;
+  double *d_planeF = nullptr, *d_planeT = nullptr;
+  int* d_unit_planes = nullptr;
+  void *ad_g = nullptr, *ad_delta = nullptr;
+  double* ad_part = nullptr;
+  unsigned int* ad_ticket = nullptr;
   bool repro = false;
   // state
   int cur = 0;  // 0: primary buffer holds the field, 1: polish buffer in FP64-18,
                 // 2: polish buffer in double-float (only inside gf_fix)
   int phase_sweeps[2] = {0, 0};
-  // graphs: one per buffer state
+  // graphs: one per buffer state (OR), one for Fourier acceleration
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph_fasd = nullptr;
   std::string err;
 };
 
@@ -227,6 +291,10 @@ void drop_graphs(gf_handle* h) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  if (h->graph_fasd) {
+    cudaGraphExecDestroy(h->graph_fasd);
+    h->graph_fasd = nullptr;
+  }
 }
 
 int cur_storage(const gf_handle* h) {
@@ -413,6 +481,106 @@ int copy_out(gf_handle* h, double* F, double* theta, double* uF, double* uT, int
   return GF_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Fourier-accelerated steepest descent (Algorithm 2)
+// ---------------------------------------------------------------------------------
+FasdArgs fasd_args(gf_handle* h, bool loop, int mode) {
+  FasdArgs a{};
+  a.links = h->links;
+  a.lat = h->lats[0];
+  a.kbuf = h->kbuf;
+  a.gbuf = h->gbuf;
+  a.plane_F = h->d_planeF;
+  a.plane_th = h->d_planeT;
+  a.unit_planes = h->d_unit_planes;
+  a.active = loop ? h->d_active : nullptr;
+  a.iters = h->d_iters;
+  a.unit_sumF = h->d_usF;
+  a.unit_sumTh = h->d_usT;
+  a.unit_F = h->d_uF;
+  a.unit_theta = h->d_uT;
+  a.lat_F = h->d_lF;
+  a.lat_theta = h->d_lT;
+  a.st = loop ? h->d_state : nullptr;
+  a.nd = h->nd;
+  a.n_units = h->n_units;
+  a.reunit = 0;
+  a.mode = mode;
+  for (int k = 0; k < 4; ++k) {
+    int l = 0;
+    while ((1 << l) < a.lat.L[k]) ++l;
+    a.logL[k] = l;
+  }
+  const double nfft = h->nd == 4 ? (double)a.lat.V : 2.0 * a.lat.V3h;
+  a.coef = 0.5 * h->alpha * (4.0 * h->nd) / nfft;
+  return a;
+}
+
+// One iteration: Delta + F/theta (A, B), then, while running, C, D, E, F.
+int enqueue_fasd_iteration(gf_handle* h, cudaStream_t s) {
+  const FasdArgs a = fasd_args(h, true, FINISH_LOOP);
+  launch_fasd_delta_xy(h->storage, h->nd, a, s);
+  GF_CK_LAUNCH(h);
+  launch_fasd_finish(a, s);
+  GF_CK_LAUNCH(h);
+  launch_fasd_zt(h->storage, h->nd, a, s);
+  GF_CK_LAUNCH(h);
+  launch_fasd_xy_inv_g(h->storage, h->nd, a, s);
+  GF_CK_LAUNCH(h);
+  launch_fasd_update(h->storage, h->nd, a, s);
+  GF_CK_LAUNCH(h);
+  launch_fasd_bump(a, s);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+int run_fasd(gf_handle* h, double eps, int budget, int* done) {
+  DevState st{};
+  st.sweep = 0;
+  st.limit = budget;
+  st.check_interval = 1;
+  st.reunit_interval = h->reunit_interval;
+  st.n_active = h->n_units;
+  st.ticket = 0;
+  st.eps = eps;
+  GF_CK(h, cudaMemcpyAsync(h->d_state, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
+  launch_fill_int(h->d_active, 1, h->n_units, h->stream);
+  GF_CK_LAUNCH(h);
+  if (!h->graph_fasd) {
+    GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = GF_OK;
+    for (int j = 0; j < kGraphSweeps && rc == GF_OK; ++j) rc = enqueue_fasd_iteration(h, h->cap_stream);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc != GF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph_fasd, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  int rc;
+  do {
+    GF_CK(h, cudaGraphLaunch(h->graph_fasd, h->stream));
+    if ((rc = read_state(h, &st)) != GF_OK) return rc;
+  } while (st.n_active > 0 && st.sweep < st.limit);
+  if (st.n_active > 0) {
+    // budget used up: F and theta of the final field (the loop measured the one before)
+    FasdArgs a = fasd_args(h, false, FINISH_MEASURE);
+    a.st = nullptr;
+    launch_fasd_delta_xy(h->storage, h->nd, a, h->stream);
+    GF_CK_LAUNCH(h);
+    a.st = h->d_state;             // the finishing kernel's ticket
+    a.active = h->d_active;        // read (for the count), not changed, in MEASURE mode
+    launch_fasd_finish(a, h->stream);
+    GF_CK_LAUNCH(h);
+  }
+  *done = st.sweep;
+  return GF_OK;
+}
+
 }  // namespace
 
 // ===================================================================================
@@ -503,6 +671,21 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   h->d_lT = (double*)(w + L.lT);
   h->d_state = (DevState*)(w + L.state);
   h->n_units = L.n_units;
+  if (h->flags & GF_FLAG_AUTOGRAD) {
+    h->ad_g = w + L.ad_g;
+    h->ad_delta = w + L.ad_delta;
+    h->ad_part = (double*)(w + L.ad_part);
+    h->ad_ticket = (unsigned int*)(w + L.ad_ticket);
+    if (cudaMemsetAsync(h->ad_ticket, 0, sizeof(unsigned int), h->stream) != cudaSuccess)
+      return bail(GF_ECUDA, "initialisation of the autograd ticket failed");
+  }
+  if (h->flags & GF_FLAG_FASD) {
+    h->kbuf = w + L.kbuf;
+    h->gbuf = w + L.gbuf;
+    h->d_planeF = (double*)(w + L.planeF);
+    h->d_planeT = (double*)(w + L.planeT);
+    h->d_unit_planes = (int*)(w + L.unit_planes);
+  }
 
   long long off = 0, off64 = 0;
   int unit = 0;
@@ -530,6 +713,19 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
       cudaGetLastError() != cudaSuccess)
     return bail(GF_ECUDA, "initialisation of the unit tables failed");
   if (build_tiles(h) != GF_OK) return bail(GF_ECUDA, h->err);
+  if (h->flags & GF_FLAG_FASD) {
+    // unit plane ranges: planes (z, t) in order; Landau one unit, Coulomb one per t
+    const LatDev& d = h->lats[0];
+    std::vector<int> up;
+    if (gauge == GF_LANDAU) up = {0, d.L[2] * d.L[3]};
+    else
+      for (int t = 0; t <= d.L[3]; ++t) up.push_back(t * d.L[2]);
+    if (cudaMemcpyAsync(h->d_unit_planes, up.data(), sizeof(int) * up.size(), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+      return bail(GF_ECUDA, "copy of the plane table failed");
+    cudaError_t e = prepare_fasd(storage, h->nd, d);
+    if (e != cudaSuccess) return bail(GF_ECUDA, std::string("Fourier kernels set-up: ") + cudaGetErrorString(e));
+  }
   *out = h;
   return GF_OK;
 }
@@ -645,6 +841,16 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
   GF_CK(h, cudaMemsetAsync(h->d_iters, 0, sizeof(int) * h->n_units, h->stream));
   h->phase_sweeps[0] = h->phase_sweeps[1] = 0;
   int rc, done = 0;
+  if (h->method == GF_METHOD_FASD) {
+    if (!(h->flags & GF_FLAG_FASD)) return fail(h, GF_ESTATE, "create the handle with GF_FLAG_FASD for Fourier acceleration");
+    if (h->cur != 0) return fail(h, GF_ESTATE, "upload the field before a Fourier-accelerated fix");
+    if ((rc = run_fasd(h, eps, maxiter, &done)) != GF_OK) return rc;
+    h->phase_sweeps[h->storage == GF_FP64_18 ? 1 : 0] = done;
+    if ((rc = copy_out(h, F, theta, nullptr, nullptr, iters)) != GF_OK) return rc;
+    DevState s{};
+    if ((rc = read_state(h, &s)) != GF_OK) return rc;
+    return s.n_active > 0 ? GF_ENOTCONVERGED : GF_OK;
+  }
   const bool mixed = (h->flags & GF_FLAG_MIXED) && h->cur == 0;
   if (mixed) {
     if ((rc = run_phase(h, std::max(eps, h->eps_switch), maxiter, &done)) != GF_OK) return rc;
@@ -735,6 +941,84 @@ int gf_set_block_size(gf_handle* h, int threads) {
   if (threads == h->threads) return GF_OK;
   h->threads = threads;
   return build_tiles(h);
+}
+
+static int ad_args(gf_handle* h, const double* c, AdArgs* a) {
+  if (!(h->flags & GF_FLAG_AUTOGRAD)) return fail(h, GF_ESTATE, "create the handle with GF_FLAG_AUTOGRAD");
+  if (h->cur != 0) return fail(h, GF_ESTATE, "upload the field first");
+  if (!c || ((uintptr_t)c % 8) != 0) return fail(h, GF_EINVAL, "c must be 8-byte aligned device memory");
+  *a = AdArgs{};
+  a->links = h->links;
+  a->lat = h->lats[0];
+  a->c = c;
+  a->g = (c64*)h->ad_g;
+  a->delta = (c64*)h->ad_delta;
+  a->part = h->ad_part;
+  a->ticket = h->ad_ticket;
+  a->nd = h->nd;
+  return GF_OK;
+}
+
+int gf_ad_functional(gf_handle* h, const double* c, double* out) {
+  if (!h) return GF_EINVAL;
+  AdArgs a;
+  int rc = ad_args(h, c, &a);
+  if (rc != GF_OK) return rc;
+  if (!out) return fail(h, GF_EINVAL, "out must be device memory for 2 doubles");
+  a.out = out;
+  launch_ad_forward(a, h->stream);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+int gf_ad_backward(gf_handle* h, const double* c, const double* upstream, double* grad) {
+  if (!h) return GF_EINVAL;
+  AdArgs a;
+  int rc = ad_args(h, c, &a);
+  if (rc != GF_OK) return rc;
+  if (!upstream || !grad) return fail(h, GF_EINVAL, "upstream and grad must be device memory");
+  a.upstream = upstream;
+  a.grad = grad;
+  launch_ad_backward(a, h->stream);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+int gf_fa_sd_step(gf_handle* h, double alpha) {
+  if (!h) return GF_EINVAL;
+  if (!(h->flags & GF_FLAG_FASD)) return fail(h, GF_ESTATE, "create the handle with GF_FLAG_FASD for Fourier acceleration");
+  if (h->cur != 0) return fail(h, GF_ESTATE, "upload the field before a Fourier-accelerated step");
+  if (!(alpha > 0.0)) return fail(h, GF_EINVAL, "alpha must be > 0");
+  const double keep = h->alpha;
+  h->alpha = alpha;
+  FasdArgs a = fasd_args(h, false, FINISH_MEASURE);
+  h->alpha = keep;
+  launch_fasd_delta_xy(h->storage, h->nd, a, h->stream);
+  GF_CK_LAUNCH(h);
+  launch_fasd_zt(h->storage, h->nd, a, h->stream);
+  GF_CK_LAUNCH(h);
+  launch_fasd_xy_inv_g(h->storage, h->nd, a, h->stream);
+  GF_CK_LAUNCH(h);
+  launch_fasd_update(h->storage, h->nd, a, h->stream);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+int gf_set_method(gf_handle* h, int method) {
+  if (!h) return GF_EINVAL;
+  if (method != GF_METHOD_OR && method != GF_METHOD_FASD) return fail(h, GF_EINVAL, "unknown method");
+  if (method == GF_METHOD_FASD && !(h->flags & GF_FLAG_FASD))
+    return fail(h, GF_ESTATE, "create the handle with GF_FLAG_FASD for Fourier acceleration");
+  h->method = method;
+  return GF_OK;
+}
+
+int gf_set_alpha(gf_handle* h, double alpha) {
+  if (!h) return GF_EINVAL;
+  if (!(alpha > 0.0)) return fail(h, GF_EINVAL, "alpha must be > 0");
+  if (alpha != h->alpha) drop_graphs(h);
+  h->alpha = alpha;
+  return GF_OK;
 }
 
 int gf_set_polish(gf_handle* h, int polish) {

@@ -303,6 +303,26 @@ __device__ __forceinline__ long long back_lexi(const LatDev& lat, const Site& s,
   }
 }
 
+// parity-split index of the site with lexicographic index lexi
+__device__ __forceinline__ int idx_from_lexi(const LatDev& lat, long long lexi) {
+  long long r = lexi;
+  const int x = (int)(r % lat.L[0]); r /= lat.L[0];
+  const int y = (int)(r % lat.L[1]); r /= lat.L[1];
+  const int z = (int)(r % lat.L[2]);
+  const int t = (int)(r / lat.L[2]);
+  return ((x + y + z + t) & 1) * lat.Vh + (int)(lexi >> 1);
+}
+
+// lexicographic index of lexi + dir * mu_hat (periodic), dir = +1 or -1
+__device__ __forceinline__ long long lexi_step(const LatDev& lat, long long lexi, int mu, int dir) {
+  long long stride = 1;
+  for (int k = 0; k < mu; ++k) stride *= lat.L[k];
+  const int c = (int)((lexi / stride) % lat.L[mu]);
+  const int L = lat.L[mu];
+  if (dir > 0) return c == L - 1 ? lexi - stride * (L - 1) : lexi + stride;
+  return c == 0 ? lexi + stride * (L - 1) : lexi - stride;
+}
+
 // ----------------------------------------------------------------------------------
 // Block reduction of doubles in a fixed order (deterministic for a given block size)
 // ----------------------------------------------------------------------------------

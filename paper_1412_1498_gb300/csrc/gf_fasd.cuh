@@ -1,0 +1,388 @@
+// gf_fasd.cuh -- Fourier-accelerated steepest descent (the paper's Algorithm 2, Eqs. (7)-(9)).
+//
+// One iteration on one lattice:
+//   A  k_fasd_delta_xy   per (z,t) plane: Delta(x) of Eq. (3) (the argument of Eq. (8)),
+//                        F / theta partials of the current field, forward FFT along x, y;
+//   B  k_fasd_finish     per unit: F, theta, stop rule (Algorithm 2 "calculate ... theta");
+//   C  k_fasd_zt         per (kx, ky): forward FFT along z (and t for Landau), the filter
+//                        (alpha/2) p^2_max / p^2 / N (k = 0 mode set to 0), inverse FFT;
+//   D  k_fasd_xy_inv_g   per (z,t) plane: inverse FFT along y, x, then
+//                        g(x) = reunit(1 + Delta~(x)) (first-order exponential, Sec. 1);
+//   E  k_fasd_update     per site: U_mu(x) <- g(x) U_mu(x) g(x+mu)^+ for every mu;
+//   F  k_fasd_bump       iteration counters.
+//
+// Delta is anti-Hermitian and traceless and the filter is real and even in k, so the
+// filtered field stays anti-Hermitian: only four complex fields are transformed -- the
+// three upper off-diagonal elements and Im Delta_00 + i Im Delta_11 -- and the other
+// elements follow from them.  FFTs are radix-2 in shared memory (extents powers of 2).
+#pragma once
+
+#include "gf_kernels.cuh"
+
+namespace gf {
+
+
+
+// ------------------------------------------------------------------------- FFT
+// In-place radix-2 FFTs of n_lines lines of length L = 2^logL in shared memory; line l
+// starts at d[(l % n_in) * in_stride + (l / n_in) * out_stride], its element k sits
+// estride further per k.  sign = -1 forward, +1 inverse (no 1/L).  tw[k] = exp(-2 pi i
+// k / L), k < L/2.  Contains __syncthreads(): call from every thread of the block.
+template <class T>
+__device__ __forceinline__ void fft_lines(cx<T>* d, const cx<T>* tw, int n_lines, int logL, int n_in,
+                                          int in_stride, int out_stride, int estride, int sign) {
+  const int L = 1 << logL;
+  const int tot = n_lines * L;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int l = i >> logL, k = i & (L - 1);
+    const int r = logL ? (int)(__brev((unsigned)k) >> (32 - logL)) : 0;
+    if (k < r) {
+      const int o = (l % n_in) * in_stride + (l / n_in) * out_stride;
+      cx<T>* a = d + o + k * estride;
+      cx<T>* b = d + o + r * estride;
+      const cx<T> t = *a;
+      *a = *b;
+      *b = t;
+    }
+  }
+  __syncthreads();
+  const int hb = tot >> 1;
+  for (int s = 1; s <= logL; ++s) {
+    const int half = 1 << (s - 1);
+    for (int i = threadIdx.x; i < hb; i += blockDim.x) {
+      const int l = i >> (logL - 1), b = i & ((L >> 1) - 1);
+      const int j = b & (half - 1), k0 = ((b >> (s - 1)) << s) + j, k1 = k0 + half;
+      cx<T> w = tw[j << (logL - s)];
+      if (sign > 0) w.im = -w.im;
+      const int o = (l % n_in) * in_stride + (l / n_in) * out_stride;
+      cx<T>* p0 = d + o + k0 * estride;
+      cx<T>* p1 = d + o + k1 * estride;
+      const cx<T> u = *p0, v = cmul(*p1, w);
+      *p0 = cadd(u, v);
+      *p1 = csub(u, v);
+    }
+    __syncthreads();
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void twiddles(cx<T>* tw, int logL) {
+  const int L = 1 << logL;
+  for (int k = threadIdx.x; k < (L >> 1); k += blockDim.x) {
+    T s, c;
+    if constexpr (sizeof(T) == 8) sincospi(-2.0 * k / L, &s, &c);
+    else sincospif(-2.0f * k / L, &s, &c);
+    tw[k] = {c, s};
+  }
+}
+
+// ------------------------------------------------------------------------- helpers
+__device__ __forceinline__ long long fwd_lexi(const LatDev& lat, const Site& s, int mu) {
+  const long long Lx = lat.L[0], LxLy = Lx * lat.L[1], V3 = LxLy * lat.L[2];
+  switch (mu) {
+    case 0: return s.x == lat.L[0] - 1 ? s.lexi - (Lx - 1) : s.lexi + 1;
+    case 1: return s.y == lat.L[1] - 1 ? s.lexi - Lx * (lat.L[1] - 1) : s.lexi + Lx;
+    case 2: return s.z == lat.L[2] - 1 ? s.lexi - LxLy * (lat.L[2] - 1) : s.lexi + LxLy;
+    default: return s.t == lat.L[3] - 1 ? s.lexi - V3 * (lat.L[3] - 1) : s.lexi + V3;
+  }
+}
+__device__ __forceinline__ int idx_of_lexi(const LatDev& lat, long long lexi) {
+  long long r = lexi;
+  const int x = (int)(r % lat.L[0]); r /= lat.L[0];
+  const int y = (int)(r % lat.L[1]); r /= lat.L[1];
+  const int z = (int)(r % lat.L[2]);
+  const int t = (int)(r / lat.L[2]);
+  return ((x + y + z + t) & 1) * lat.Vh + (int)(lexi >> 1);
+}
+__device__ __forceinline__ bool fasd_running(const DevState* st) {
+  return st == nullptr || (st->n_active > 0 && st->sweep < st->limit);
+}
+
+// g rows 0, 1 in the links' precision: FP32 as 3 float4 words, FP64 as 6 double2 words
+template <class T>
+__device__ __forceinline__ void g_store(char* gbuf, long long V, int idx, const cx<T> (&g)[9]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* p = reinterpret_cast<float4*>(gbuf);
+#pragma unroll
+    for (int w = 0; w < 3; ++w) p[w * V + idx] = make_float4(g[2 * w].re, g[2 * w].im, g[2 * w + 1].re, g[2 * w + 1].im);
+  } else {
+    double2* p = reinterpret_cast<double2*>(gbuf);
+#pragma unroll
+    for (int w = 0; w < 6; ++w) p[w * V + idx] = make_double2(g[w].re, g[w].im);
+  }
+}
+template <class T>
+__device__ __forceinline__ void g_load(const char* gbuf, long long V, int idx, cx<T> (&g)[9]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(gbuf);
+#pragma unroll
+    for (int w = 0; w < 3; ++w) {
+      const float4 v = p[w * V + idx];
+      g[2 * w] = {v.x, v.y};
+      g[2 * w + 1] = {v.z, v.w};
+    }
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(gbuf);
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+      const double2 v = p[w * V + idx];
+      g[w] = {v.x, v.y};
+    }
+  }
+  third_row(g, g + 6);
+}
+
+// ------------------------------------------------------------------------- A: Delta + FFT xy
+template <int S, int ND>
+__global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  constexpr int NE = St::NE;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double red[64];
+  __shared__ cx<T> twx[32], twy[32];
+  if (a.st && a.st->n_active <= 0) return;
+  const LatDev& lat = a.lat;
+  const int z = blockIdx.x, t = blockIdx.y;
+  const int Lx = lat.L[0], Ly = lat.L[1], P = Lx * Ly;
+  cx<T>* pl = reinterpret_cast<cx<T>*>(smraw);  // [4][Ly][Lx]
+  twiddles(twx, a.logL[0]);
+  twiddles(twy, a.logL[1]);
+  T fsum = T(0), q = T(0);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const int x = i % Lx, y = i / Lx;
+    Site s;
+    s.x = x; s.y = y; s.z = z; s.t = t;
+    s.lexi = x + (long long)Lx * (y + (long long)Ly * (z + (long long)lat.L[2] * t));
+    const int idx = ((x + y + z + t) & 1) * lat.Vh + (int)(s.lexi >> 1);
+    const char* base = a.links + lat.off_bytes;
+    cx<T> A[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
+#pragma unroll
+    for (int nu = 0; nu < ND; ++nu) {
+      cx<T> f[NE], b[NE];
+      St::load(base, lat.V, nu, idx, f);
+      St::load(base, lat.V, nu, idx_of_lexi(lat, back_lexi(lat, s, nu)), b);
+      fsum = fsum + re_trace(f);   // forward links only: every link once over all sites
+      add_to_A(A, f, b);
+    }
+    // Delta = A - A^+ - tr/3 (as theta_site) and its four independent complex fields
+    cx<T> D[9];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) D[3 * r + c] = csub(A[3 * r + c], cconj(A[3 * c + r]));
+    const cx<T> sum = cadd(cadd(D[0], D[4]), D[8]);
+    const cx<T> tr = {sum.re / T(3), sum.im / T(3)};
+    D[0] = csub(D[0], tr);
+    D[4] = csub(D[4], tr);
+    D[8] = csub(D[8], tr);
+    T qq = T(0);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) qq = qq + (D[e].re * D[e].re + D[e].im * D[e].im);
+    q = q + qq;
+    pl[0 * P + i] = D[1];
+    pl[1 * P + i] = D[2];
+    pl[2 * P + i] = D[5];
+    pl[3 * P + i] = {D[0].im, D[4].im};
+  }
+  const T v[2] = {fsum, q};
+  double o[2];
+  tile_sum<T, 2>(v, o, red);
+  if (threadIdx.x == 0) {
+    a.plane_F[z + lat.L[2] * t] = o[0];
+    a.plane_th[z + lat.L[2] * t] = o[1];
+  }
+  __syncthreads();
+  // forward FFT along x (rows), then along y (columns), all four fields
+  fft_lines(pl, twx, 4 * Ly, a.logL[0], 1, 0, Lx, 1, -1);       // rows (f, y), along x
+  fft_lines(pl, twy, 4 * Lx, a.logL[1], Lx, 1, P, Lx, -1);       // columns (f, x), along y
+  cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf);
+  const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
+  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+    const int f = i / P, j = i % P;
+    kb[f * lat.V + plane0 + j] = pl[i];
+  }
+}
+
+// ------------------------------------------------------------------------- B: finish
+__global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
+  __shared__ double red[96];
+  __shared__ int s_last;
+  if (a.st && a.st->n_active <= 0 && a.mode == FINISH_LOOP) return;
+  const int u = blockIdx.x;
+  const bool was_active = a.active == nullptr || a.active[u] != 0;
+  if (a.mode != FINISH_LOOP || was_active) {
+    const int pb = a.unit_planes[u], pe = a.unit_planes[u + 1];
+    double v[2] = {0.0, 0.0};
+    for (int i = pb + (int)threadIdx.x; i < pe; i += blockDim.x) {
+      v[0] += a.plane_F[i];
+      v[1] += a.plane_th[i];
+    }
+    double w[3] = {v[0], v[1], 0.0};
+    block_sum<3>(w, red);
+    if (threadIdx.x == 0) {
+      const double vol = a.nd == 4 ? (double)a.lat.V : 2.0 * a.lat.V3h;
+      a.unit_sumF[u] = w[0];
+      a.unit_sumTh[u] = w[1];
+      a.unit_F[u] = w[0] / ((double)a.nd * 3.0 * vol);
+      a.unit_theta[u] = w[1] / (3.0 * vol);
+      if (a.mode == FINISH_LOOP && a.active) a.active[u] = a.unit_theta[u] >= a.st->eps;
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&a.st->ticket, 1u) == (unsigned int)(a.n_units - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) {
+    double sF = 0.0, sT = 0.0;
+    for (int k = 0; k < a.n_units; ++k) {
+      sF += __ldcg(a.unit_sumF + k);
+      sT += __ldcg(a.unit_sumTh + k);
+    }
+    a.lat_F[0] = sF / ((double)a.nd * 3.0 * (double)a.lat.V);
+    a.lat_theta[0] = sT / (3.0 * (double)a.lat.V);
+  }
+  double c[1] = {0.0};
+  if (a.active)
+    for (int k = threadIdx.x; k < a.n_units; k += blockDim.x) c[0] += (double)__ldcg(a.active + k);
+  block_sum<1>(c, red);
+  if (threadIdx.x == 0) {
+    if (a.mode == FINISH_LOOP && a.active) a.st->n_active = (int)c[0];
+    a.st->ticket = 0u;
+  }
+}
+
+// ------------------------------------------------------------------------- C: FFT z(t), filter
+// Block: one ky, KX consecutive kx, and (Coulomb) one t; loops over the four fields.
+template <class T, int ND>
+__global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ cx<T> twz[32], twt[32];
+  if (!fasd_running(a.st)) return;
+  const LatDev& lat = a.lat;
+  const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2], Lt = lat.L[3];
+  const int KX = Lx < 4 ? Lx : 4;
+  const int kx0 = blockIdx.x * KX, ky = blockIdx.y;
+  const int t0 = ND == 4 ? 0 : (int)blockIdx.z, nt = ND == 4 ? Lt : 1;
+  if (ND == 3 && a.active && !a.active[t0]) return;
+  cx<T>* col = reinterpret_cast<cx<T>*>(smraw);  // [nt][Lz][KX]
+  twiddles(twz, a.logL[2]);
+  if (ND == 4) twiddles(twt, a.logL[3]);
+  __syncthreads();
+  cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf);
+  const long long P = (long long)Lx * Ly;
+  const int n = nt * Lz * KX;
+  for (int f = 0; f < 4; ++f) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int kxl = i % KX, z = (i / KX) % Lz, tl = i / (KX * Lz);
+      col[i] = kb[f * lat.V + P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl];
+    }
+    __syncthreads();
+    // col[kxl + KX (z + Lz tl)]: along z the lines are (kxl, tl), along t they are (kxl, z)
+    fft_lines(col, twz, nt * KX, a.logL[2], KX, 1, Lz * KX, KX, -1);
+    if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, Lz * KX, -1);
+    // filter
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int kxl = i % KX, kz = (i / KX) % Lz, kt = i / (KX * Lz);
+      T p2 = T(0), sn;
+      sn = sinpi((T)(kx0 + kxl) / (T)Lx); p2 += T(4) * sn * sn;
+      sn = sinpi((T)ky / (T)Ly);          p2 += T(4) * sn * sn;
+      sn = sinpi((T)kz / (T)Lz);          p2 += T(4) * sn * sn;
+      if (ND == 4) { sn = sinpi((T)kt / (T)Lt); p2 += T(4) * sn * sn; }
+      const T fac = p2 > T(0) ? (T)a.coef / p2 : T(0);
+      col[i] = cscale(col[i], fac);
+    }
+    __syncthreads();
+    if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, Lz * KX, +1);
+    fft_lines(col, twz, nt * KX, a.logL[2], KX, 1, Lz * KX, KX, +1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int kxl = i % KX, z = (i / KX) % Lz, tl = i / (KX * Lz);
+      kb[f * lat.V + P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl] = col[i];
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------- D: inverse xy, g
+template <int S, int ND>
+__global__ void __launch_bounds__(256) k_fasd_xy_inv_g(FasdArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ cx<T> twx[32], twy[32];
+  if (!fasd_running(a.st)) return;
+  const LatDev& lat = a.lat;
+  const int z = blockIdx.x, t = blockIdx.y;
+  if (ND == 3 && a.active && !a.active[t]) return;
+  const int Lx = lat.L[0], Ly = lat.L[1], P = Lx * Ly;
+  cx<T>* pl = reinterpret_cast<cx<T>*>(smraw);
+  twiddles(twx, a.logL[0]);
+  twiddles(twy, a.logL[1]);
+  const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf);
+  const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
+  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) pl[i] = kb[(i / P) * lat.V + plane0 + i % P];
+  __syncthreads();
+  fft_lines(pl, twy, 4 * Lx, a.logL[1], Lx, 1, P, Lx, +1);
+  fft_lines(pl, twx, 4 * Ly, a.logL[0], 1, 0, Lx, 1, +1);
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    const int x = i % Lx, y = i / Lx;
+    const long long lexi = x + (long long)Lx * (y + (long long)Ly * (z + (long long)lat.L[2] * t));
+    const int idx = ((x + y + z + t) & 1) * lat.Vh + (int)(lexi >> 1);
+    // Delta~ (already scaled by alpha/2 p^2_max/p^2/N): anti-Hermitian, traceless
+    const cx<T> d01 = pl[i], d02 = pl[P + i], d12 = pl[2 * P + i], dd = pl[3 * P + i];
+    cx<T> g[9];
+    g[0] = {T(1), dd.re};
+    g[4] = {T(1), dd.im};
+    g[8] = {T(1), -(dd.re + dd.im)};
+    g[1] = d01; g[2] = d02; g[5] = d12;
+    g[3] = cneg(cconj(d01)); g[6] = cneg(cconj(d02)); g[7] = cneg(cconj(d12));
+    reunit(g);
+    g_store<T>(a.gbuf, lat.V, idx, g);
+  }
+}
+
+// ------------------------------------------------------------------------- E: update
+template <int S, int ND>
+__global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
+  using St = Store<S>;
+  using T = typename St::T;
+  constexpr int NE = St::NE;
+  if (!fasd_running(a.st)) return;
+  const LatDev& lat = a.lat;
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= lat.V) return;
+  const int p = i >= lat.Vh ? 1 : 0;
+  const int h = (int)(i - (long long)p * lat.Vh);
+  const Site s = site_of(lat, p, h);
+  if (ND == 3 && a.active && !a.active[s.t]) return;
+  const bool reunit_now = a.st ? state_reunit_sweep(a.st) : a.reunit != 0;
+  char* base = a.links + lat.off_bytes;
+  cx<T> g[9];
+  g_load<T>(a.gbuf, lat.V, (int)i, g);
+#pragma unroll 1
+  for (int mu = 0; mu < 4; ++mu) {
+    cx<T> u[NE], gn[9];
+    St::load(base, lat.V, mu, (int)i, u);
+    g_load<T>(a.gbuf, lat.V, idx_of_lexi(lat, fwd_lexi(lat, s, mu)), gn);
+    left_mul(g, u);
+    right_mul_dag(u, gn);
+    if (reunit_now) reunit(u);
+    St::store(base, lat.V, mu, (int)i, u);
+  }
+}
+
+// ------------------------------------------------------------------------- F: counters
+__global__ void k_fasd_bump(FasdArgs a) {
+  if (a.st == nullptr || a.active == nullptr || !fasd_running(a.st)) return;
+  for (int u = threadIdx.x; u < a.n_units; u += blockDim.x)
+    if (a.active[u]) a.iters[u] += 1;
+  __syncthreads();
+  if (threadIdx.x == 0) a.st->sweep += 1;
+}
+
+}  // namespace gf

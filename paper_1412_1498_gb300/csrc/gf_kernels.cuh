@@ -218,6 +218,49 @@ struct FinishArgs {
 
 enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2 };
 
+// Fourier-accelerated steepest descent (kernels in gf_fasd.cuh)
+struct FasdArgs {
+  char* links;            // link storage (FP32-12 or FP64-18) of the lattice
+  LatDev lat;
+  void* kbuf;             // 4 complex fields, [f][t][z][y][x]
+  char* gbuf;             // g(x): rows 0 and 1, 2 * 3 complex elements, planes [w][idx]
+  double* plane_F;        // per (z, t) plane
+  double* plane_th;
+  const int* unit_planes; // n_units + 1 plane boundaries
+  int* active;
+  int* iters;
+  double* unit_sumF;
+  double* unit_sumTh;
+  double* unit_F;
+  double* unit_theta;
+  double* lat_F;
+  double* lat_theta;
+  DevState* st;           // nullable for a single step
+  int nd;                 // 4 Landau, 3 Coulomb
+  int n_units;
+  int reunit;             // reunitarise the links in the update (single-step use)
+  int mode;               // finish: FINISH_LOOP or FINISH_MEASURE
+  int logL[4];
+  double coef;            // alpha / 2 * p^2_max / N_fft
+};
+
+// Differentiable F(c), theta(c) (kernels in gf_autograd.cuh)
+using c64 = cx<double>;
+
+struct AdArgs {
+  const char* links;   // FP64-18 storage of the lattice
+  LatDev lat;
+  const double* c;     // [V][8], canonical site order
+  c64* g;              // [V][9] scratch
+  c64* delta;          // [V][9] scratch
+  double* part;        // [blocks][2]
+  double* out;         // F, theta
+  const double* upstream;  // dL/dF, dL/dtheta
+  double* grad;        // [V][8]
+  unsigned int* ticket;
+  int nd;
+};
+
 // ----------------------------------------------------------------------------------
 // Algorithm 1, one half-sweep: every site of one parity, one thread per site.
 // KEEP: hold the 8 links in registers (FP32); otherwise stream them twice (FP64).

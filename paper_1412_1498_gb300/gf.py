@@ -33,6 +33,9 @@ GF_OK, GF_ENOTCONVERGED, GF_EINVAL, GF_ECUDA, GF_ENOMEM, GF_ESTATE = 0, 1, -1, -
 GF_LANDAU, GF_COULOMB = 0, 1
 GF_FP64_18, GF_FP32_18, GF_FP32_12 = 0, 1, 2
 GF_FLAG_MIXED = 1
+GF_FLAG_FASD = 2
+GF_FLAG_AUTOGRAD = 4
+GF_METHOD_OR, GF_METHOD_FASD = 0, 1
 GF_OR_FIRST_ORDER, GF_OR_EXACT = 0, 1
 GF_SWEEP_AUTO, GF_SWEEP_REGISTER, GF_SWEEP_PIPELINED = 0, 1, 2
 GF_POLISH_FP64, GF_POLISH_SPLIT = 0, 1
@@ -64,6 +67,11 @@ _SIGS = {
     "gf_fix_phase_sweeps": (_int, [_vp, _IP, _IP]),
     "gf_set_sweep_variant": (_int, [_vp, _int]),
     "gf_set_polish": (_int, [_vp, _int]),
+    "gf_fa_sd_step": (_int, [_vp, _dbl]),
+    "gf_set_method": (_int, [_vp, _int]),
+    "gf_set_alpha": (_int, [_vp, _dbl]),
+    "gf_ad_functional": (_int, [_vp, _vp, _vp]),
+    "gf_ad_backward": (_int, [_vp, _vp, _vp, _vp]),
     "gf_functional_theta_noalloc": (_int, [_IP, _int, _vp, _vp, _vp]),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -200,6 +208,26 @@ def gf_set_block_size(h, threads: int) -> None:
     _check(_lib.gf_set_block_size(h, threads), h)
 
 
+def gf_fa_sd_step(h, alpha: float = 0.08) -> None:
+    _check(_lib.gf_fa_sd_step(h, alpha), h)
+
+
+def gf_set_method(h, method: int) -> None:
+    _check(_lib.gf_set_method(h, method), h)
+
+
+def gf_set_alpha(h, alpha: float) -> None:
+    _check(_lib.gf_set_alpha(h, alpha), h)
+
+
+def gf_ad_functional(h, c_ptr: int, out_ptr: int) -> None:
+    _check(_lib.gf_ad_functional(h, _vp(c_ptr or None), _vp(out_ptr or None)), h)
+
+
+def gf_ad_backward(h, c_ptr: int, upstream_ptr: int, grad_ptr: int) -> None:
+    _check(_lib.gf_ad_backward(h, _vp(c_ptr or None), _vp(upstream_ptr or None), _vp(grad_ptr or None)), h)
+
+
 def gf_set_polish(h, polish: int) -> None:
     _check(_lib.gf_set_polish(h, polish), h)
 
@@ -241,11 +269,12 @@ class GaugeFixer:
     """One handle over one lattice or a batch; memory and stream from torch."""
 
     def __init__(self, dims, gauge: int = GF_LANDAU, storage: int = GF_FP32_12, mixed: bool = False,
-                 device=None, stream=None):
+                 device=None, stream=None, fasd: bool = False, autograd: bool = False):
         import torch
         self.dims_list = [tuple(int(v) for v in d) for d in (dims if isinstance(dims[0], (list, tuple)) else [dims])]
         self.device = torch.device(device if device is not None else "cuda")
-        flags = GF_FLAG_MIXED if mixed else 0
+        flags = ((GF_FLAG_MIXED if mixed else 0) | (GF_FLAG_FASD if fasd else 0)
+                 | (GF_FLAG_AUTOGRAD if autograd else 0))
         nbytes = gf_workspace_bytes(self.dims_list, gauge, storage, flags)
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -392,3 +392,77 @@ def check_coulomb_per_slice_masks_freeze_converged_slices(orc):
     assert np.all(th_t < 1e-12)
     assert len(set(r["slice_iters"].tolist())) > 1      # slices stop at different sweeps
     assert r["iters"] == r["slice_iters"].max()
+
+
+# --- Eqs. (7)-(9), Algorithm 2: Fourier-accelerated steepest descent ------------------
+
+def _laplacian(f, axes):
+    # -d^2 f(x) = sum_mu [2 f(x) - f(x + mu) - f(x - mu)]   (position space, no FFT)
+    return sum(2 * f - np.roll(f, -1, axis=a) - np.roll(f, 1, axis=a) for a in axes)
+
+
+def check_fasd_filter_inverts_laplacian(orc, gauge):
+    # Delta~ = F^-1 (p^2max / p^2) F Delta solves -d^2 Delta~ = p^2max Delta (Delta has no
+    # zero mode): pins p^2 as the eigenvalues of -d^2, the FFT axes and normalisation
+    from oracle import fasd
+    dims = (4, 8, 4, 6)
+    U = fields.random_gauge_config(dims, 0.5, 90)
+    D = orc.delta(U, gauge)
+    Dt = fasd.filtered_delta(D, gauge)
+    axes = (0, 1, 2, 3) if gauge == orc.LANDAU else (1, 2, 3)
+    nd = 4 if gauge == orc.LANDAU else 3
+    assert np.abs(_laplacian(Dt, axes) - 4 * nd * D).max() < 1e-12
+    # and Delta~ keeps Delta's algebra: anti-Hermitian, traceless
+    assert np.abs(Dt + obs.dag(Dt)).max() < 1e-13
+    assert np.abs(np.trace(Dt, axis1=-2, axis2=-1)).max() < 1e-13
+
+
+def check_fasd_unit_filter_is_naive_descent(orc, gauge):
+    # with the filter replaced by 1, Algorithm 2's step is the naive step of Eq. (7)
+    from oracle import fasd
+    U = fields.random_gauge_config((4, 4, 4, 4), 0.5, 91)
+    a = fasd.fa_sd_step(U, 0.08, gauge, kind="none", delta_fn=orc.delta)
+    b = fasd.sd_step(U, 0.08, gauge, delta_fn=orc.delta)
+    assert np.abs(a - b).max() < 1e-14
+
+
+def check_fasd_ascends_and_is_gauge_transformation(orc, gauge):
+    from oracle import fasd
+    U = fields.random_gauge_config((4, 4, 6, 4), 0.5, 92)
+    F0 = orc.measure(U, gauge)[0]
+    W = fasd.fa_sd_step(U, 0.01, gauge, delta_fn=orc.delta)
+    assert orc.measure(W, gauge)[0] > F0
+    W = U
+    for _ in range(5):
+        W = fasd.fa_sd_step(W, 0.08, gauge, delta_fn=orc.delta)
+    assert obs.unitarity_error(W) < 1e-13 and obs.det_error(W) < 1e-13
+    assert np.abs(obs.plaquettes(W) - obs.plaquettes(U)).max() < 1e-12
+    assert np.abs(obs.polyakov(W) - obs.polyakov(U)).max() < 1e-12
+
+
+def check_fasd_coulomb_slices_independent(orc):
+    # Coulomb gauge transforms each time slice in 3D: a slice evolves as if alone
+    from oracle import fasd
+    dims = (4, 4, 4, 4)
+    U = fields.random_gauge_config(dims, 0.5, 93)
+    W = U
+    for _ in range(3):
+        W = fasd.fa_sd_step(W, 0.08, orc.COULOMB, delta_fn=orc.delta)
+    for t in range(dims[3]):
+        S = np.broadcast_to(np.eye(3, dtype=complex), (2,) + U.shape[1:]).copy()
+        S[t % 2] = U[t]
+        S[1 - t % 2] = U[t]       # same slice twice: each slice of S evolves like U[t]
+        for _ in range(3):
+            S = fasd.fa_sd_step(S, 0.08, orc.COULOMB, delta_fn=orc.delta)
+        assert np.abs(S[t % 2][..., :3, :, :] - W[t][..., :3, :, :]).max() < 1e-12
+
+
+def check_fasd_converges_faster_than_or(orc):
+    # Sec. 4: steepest descent with Fourier acceleration converges in fewer iterations
+    # than overrelaxation (8^4 workload, eps 0.4, seeds 1 / 2)
+    from oracle import fasd
+    U = fields.random_gauge_config((8, 8, 8, 8), 0.4, 1, 2)
+    _, r = fasd.fa_sd_fix(U.copy(), 1e-12, 1000, 0.08)
+    r_or = orc.fix(U.copy(), 1e-12, 1000, 1.7)
+    assert r["rc"] == 0 and r_or["rc"] == 0
+    assert r["iters"] < r_or["iters"], (r["iters"], r_or["iters"])

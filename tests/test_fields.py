@@ -24,11 +24,18 @@ def test_gell_mann_algebra():
 
 def test_expi_matches_library_expm():
     rng = np.random.default_rng(0)
-    for _ in range(20):
-        c = rng.standard_normal(8)
-        A = np.einsum("a,aij->ij", c, fields.gell_mann())
-        ref = scipy.linalg.expm(1j * 0.7 * A)
-        assert np.abs(fields.expi_hermitian(A[None], 0.7)[0] - ref).max() < 1e-13
+    for scale in (1e-9, 1e-3, 0.7, 3.0):
+        for _ in range(20):
+            c = rng.standard_normal(8)
+            A = np.einsum("a,aij->ij", c, fields.gell_mann())
+            ref = scipy.linalg.expm(1j * scale * A)
+            assert np.abs(fields.expi_hermitian(A[None], scale)[0] - ref).max() < 1e-13
+            assert np.abs(fields.expi_hermitian_eigh(A[None], scale)[0] - ref).max() < 1e-13
+    # both signs of det and degenerate spectra
+    for A in (np.diag([1.0, 1.0, -2.0]), np.diag([-1.0, -1.0, 2.0]), np.zeros((3, 3)), fields.gell_mann()[2]):
+        A = A.astype(complex)
+        ref = scipy.linalg.expm(1j * 0.9 * A)
+        assert np.abs(fields.expi_hermitian(A[None], 0.9)[0] - ref).max() < 1e-13
 
 
 def test_smooth_field_is_su3_and_deterministic():

@@ -1,0 +1,141 @@
+"""The CUDA path at the workloads' full sizes (needs a GB300).
+
+Checks use what the oracle can compute at these sizes (one sweep, F and theta of a
+downloaded field) or properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_1498_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def gf():
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1412_1498_gb300 import build
+    build.build()
+    from paper_1412_1498_gb300 import gf as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def field_32x4():
+    return fields.random_gauge_config((32, 32, 32, 32), 0.5, 3)
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_32x4_sweep_against_oracle(gf, field_32x4, storage):
+    # the bench workload (32^4, eps 0.5, seed 3) in the bench's launch configuration
+    dims = (32, 32, 32, 32)
+    fx = gf.GaugeFixer(dims, gf.GF_LANDAU, storage)
+    fx.upload(field_32x4)
+    start = fx.download()
+    out = fx.fix(1e-300, 1)                       # one sweep + F/theta (graph path)
+    got = fx.download()
+    ref = start.copy()
+    oracle.sweep(ref, 1.7)
+    err = np.abs(got - ref).max()
+    assert err < (1e-13 if storage == gf.GF_FP64_18 else 5e-6), err
+    F, th, _, _ = oracle.measure(got)
+    tol = 1e-12 if storage == gf.GF_FP64_18 else 1e-5
+    assert abs(out["F"][0] - F) <= tol * abs(F) and abs(out["theta"][0] - th) <= tol * th
+    fx.close()
+
+
+def _verify_units(out, unit_theta, oracle_theta, eps):
+    """Per-unit stop rule at full size: the oracle's theta of every unit's final field equals
+    the GPU's, the units the GPU reports below eps are below eps for the oracle, and the
+    return status says whether every unit converged."""
+    assert np.allclose(unit_theta, oracle_theta, rtol=1e-9, atol=0)
+    done = unit_theta < eps
+    assert np.all(oracle_theta[done] < eps * (1 + 1e-9))
+    assert (out["rc"] == 0) == bool(np.all(done))
+    return int(done.sum())
+
+
+def test_coulomb_32x3x64_mixed_per_slice(gf):
+    # Coulomb gauge 32^3 x 64, eps 0.5, seed 4: 64 slices fixed in one launch with
+    # per-slice theta and masks, FP32 bulk then double-float polish, stop at
+    # theta_t < 1e-15 per slice.  With omega = 1.7 the slowest slices of this field need
+    # far more sweeps than the others (the oracle shows the same spread on smaller
+    # slices), so the run has a fixed budget and every slice is checked by the oracle.
+    dims = (32, 32, 32, 64)
+    budget = 30000
+    U = fields.random_gauge_config(dims, 0.5, 4)
+    fx = gf.GaugeFixer(dims, gf.GF_COULOMB, gf.GF_FP32_12, mixed=True)
+    gf.gf_set_polish(fx.h, gf.GF_POLISH_SPLIT)
+    fx.upload(U)
+    out = fx.fix(1e-15, budget)
+    _, _, _, uT = fx.functional_theta()
+    got = fx.download()
+    fx.close()
+    F, th, F_t, th_t = oracle.measure(got, oracle.COULOMB)
+    n = _verify_units(out, uT, th_t, 1e-15)
+    print(f"coulomb 32^3x64: {n}/64 slices below 1e-15 within {budget} sweeps; sweeps per slice "
+          f"min {out['iters'].min()} max {out['iters'].max()}, phases {out['phase_sweeps']}")
+
+
+def test_ensemble_48_configs_one_batch(gf):
+    # 16 x 16^4 + 16 x 24^4 + 16 x 16^3x32, eps ~ U[0.3, 0.6], seeds 100..147, one batch,
+    # FP32 then double-float polish to theta < 1e-15 per configuration, fixed budget
+    import time
+    dims_list = [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 24)] * 16 + [(16, 16, 16, 32)] * 16
+    seeds = list(range(100, 148))
+    budget = 20000
+    Us = fields.ensemble(dims_list, seeds)
+    fb = gf.GaugeFixer(dims_list, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True)
+    gf.gf_set_polish(fb.h, gf.GF_POLISH_SPLIT)
+    for i, U in enumerate(Us):
+        fb.upload(U, i)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ob = fb.fix(1e-15, budget)
+    el = time.perf_counter() - t0
+    _, _, _, uT = fb.functional_theta()
+    th_o = np.array([oracle.measure(fb.download(i))[1] for i in range(48)])
+    n = _verify_units(ob, uT, th_o, 1e-15)
+    unit_sweeps = int(ob["iters"].sum())
+    print(f"ensemble: {n}/48 below 1e-15; {unit_sweeps} unit-sweeps in {el:.2f} s = "
+          f"{unit_sweeps / el:.0f} unit-sweeps/s; phases {ob['phase_sweeps']}")
+    fb.close()
+
+
+def test_batch_member_equals_alone_fp32(gf):
+    # one 16^4, one 24^4, one 16^3x32 member of the ensemble: batched FP32 fixing with
+    # per-unit masks gives each member the bits and sweep count of its run alone
+    dims_list = [(16, 16, 16, 16), (24, 24, 24, 24), (16, 16, 16, 32)]
+    seeds = [100, 116, 132]
+    Us = fields.ensemble(dims_list, seeds)
+    fb = gf.GaugeFixer(dims_list, gf.GF_LANDAU, gf.GF_FP32_12)
+    for i, U in enumerate(Us):
+        fb.upload(U, i)
+    ob = fb.fix(1e-6, 4000)
+    for i in range(3):
+        fa = gf.GaugeFixer(dims_list[i], gf.GF_LANDAU, gf.GF_FP32_12)
+        fa.upload(Us[i])
+        oa = fa.fix(1e-6, 4000)
+        assert oa["iters"][0] == ob["iters"][i]
+        assert np.array_equal(fa.download(), fb.download(i))
+        assert oa["theta"][0] == ob["theta"][i]
+        fa.close()
+    fb.close()
+
+
+def test_large_lattice_relaxation_never_decreases_F(gf):
+    # 48^4 (5.3 M sites, 1 GB of FP32-12 links): omega = 1 sweeps never lower F
+    dims = (48, 48, 48, 48)
+    V = 48 ** 4
+    U = fields.random_gauge_config((48, 48, 48, 4), 0.5, 9)   # generate one slab ...
+    fx = gf.GaugeFixer(dims, gf.GF_LANDAU, gf.GF_FP32_12)
+    fx.upload(np.ascontiguousarray(np.tile(U, (12, 1, 1, 1, 1, 1, 1))))   # ... tiled along t
+    F_prev = fx.functional_theta()[0][0]
+    for k in range(6):
+        gf.gf_or_sweep(fx.h, k % 2, 1.0)
+        F = fx.functional_theta()[0][0]
+        assert F >= F_prev - 2e-7 * abs(F_prev), (k, F, F_prev)
+        F_prev = F
+    fx.close()

@@ -3,6 +3,8 @@ pins catch every one of them.  Each mutant is a textual edit of gf_oracle.c comp
 into a temporary library; at least one pin must fail on it."""
 import os
 
+import numpy as np
+
 import pytest
 
 import oracle
@@ -55,4 +57,43 @@ def test_pins_catch_planted_mistake(name, orig, bad, tmp_path):
             check(mut, *args)
         except (AssertionError, ValueError, FloatingPointError):
             return  # caught
+    pytest.fail(f"no pin caught the planted mistake {name}")
+
+
+# planted mistakes in the Fourier-accelerated steepest descent oracle (oracle/fasd.py)
+FASD_MUTANTS = [
+    ("p2_sin_not_squared", "s = 4.0 * np.sin(np.pi * k / L) ** 2", "s = 4.0 * np.sin(np.pi * k / L)"),
+    ("p2_wrong_period", "s = 4.0 * np.sin(np.pi * k / L) ** 2", "s = 4.0 * np.sin(2 * np.pi * k / L) ** 2"),
+    ("p2max_always_16", "p2max = 4.0 * _nd(gauge)", "p2max = 16.0"),
+    ("ifft_is_fft", "out[..., i, j] = np.fft.ifftn(Fk, axes=axes)", "out[..., i, j] = np.fft.fftn(Fk, axes=axes) / Fk[..., 0, 0, 0].size"),
+    ("coulomb_fft_over_t", "_AXES = {0: (0, 1, 2, 3), 1: (1, 2, 3)}", "_AXES = {0: (0, 1, 2, 3), 1: (0, 1, 2, 3)}"),
+    ("half_alpha_dropped", "g = np.eye(3, dtype=np.complex128) + 0.5 * alpha * Dt", "g = np.eye(3, dtype=np.complex128) + alpha * Dt"),
+    ("update_no_dagger", "out[..., mu, :, :] = g @ U[..., mu, :, :] @ np.roll(gd, -1, axis=ax)",
+     "out[..., mu, :, :] = g @ U[..., mu, :, :] @ np.roll(g, -1, axis=ax)"),
+    ("update_backward_neighbour", "np.roll(gd, -1, axis=ax)", "np.roll(gd, 1, axis=ax)"),
+]
+
+FASD_CASES = [c for c in CASES if c[0].__name__.startswith("check_fasd")]
+
+
+@pytest.mark.parametrize("name,orig,bad", FASD_MUTANTS, ids=[m[0] for m in FASD_MUTANTS])
+def test_fasd_pins_catch_planted_mistake(name, orig, bad, tmp_path, monkeypatch):
+    import importlib.util
+    import sys
+    src = os.path.join(os.path.dirname(oracle.__file__), "fasd.py")
+    text = open(src).read()
+    assert text.count(orig) >= 1, f"mutation site for {name} missing"
+    path = tmp_path / "fasd_mut.py"
+    path.write_text(text.replace(orig, bad))
+    spec = importlib.util.spec_from_file_location("oracle.fasd", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    monkeypatch.setitem(sys.modules, "oracle.fasd", mod)
+    monkeypatch.setattr(oracle, "fasd", mod, raising=False)
+    for check, args in FASD_CASES:
+        try:
+            with np.errstate(all="ignore"):
+                check(oracle, *args)
+        except (AssertionError, ValueError, FloatingPointError, ZeroDivisionError):
+            return
     pytest.fail(f"no pin caught the planted mistake {name}")

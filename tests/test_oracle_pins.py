@@ -34,6 +34,14 @@ CASES = [
     (C.check_smooth_field_recovered_functional, ()),
     (C.check_coulomb_slices_fix_independently, ()),
     (C.check_coulomb_per_slice_masks_freeze_converged_slices, ()),
+    (C.check_fasd_filter_inverts_laplacian, (L,)),
+    (C.check_fasd_filter_inverts_laplacian, (CO,)),
+    (C.check_fasd_unit_filter_is_naive_descent, (L,)),
+    (C.check_fasd_unit_filter_is_naive_descent, (CO,)),
+    (C.check_fasd_ascends_and_is_gauge_transformation, (L,)),
+    (C.check_fasd_ascends_and_is_gauge_transformation, (CO,)),
+    (C.check_fasd_coulomb_slices_independent, ()),
+    (C.check_fasd_converges_faster_than_or, ()),
 ]
 
 
