@@ -201,22 +201,8 @@ def run_gpu(args):
     gf.gf_set_reunit_interval(fx.h, 20)
     fx.upload(U)
 
-    # ---- block size: pick the fastest half-sweep launch shape (64 / 128 / 256 threads)
-    best = None
-    for threads in (64, 128, 256):
-        gf.gf_set_block_size(fx.h, threads)
-        for _ in range(3):
-            fx.or_sweep(2, OMEGA)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(10):
-            fx.or_sweep(2, OMEGA)
-        e1.record(stream)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / 20
-        if best is None or ms < best[1]:
-            best = (threads, ms)
-    gf.gf_set_block_size(fx.h, best[0])
+    # ---- launch shape: the library's autotuner times every block size / kernel variant
+    best = gf.gf_autotune(fx.h)
     fx.upload(U)
 
     # ---- warm-up steps (untimed)
@@ -308,6 +294,50 @@ def run_gpu(args):
         f3.close()
         del f3
 
+    # ---- Fourier-accelerated steepest descent (Algorithm 2), 32^4 FP32, seed 5, alpha 0.08
+    fasd = None
+    if args.fasd_iters > 0:
+        U5 = make_field(DIMS, EPS_FIELD, 5)
+        f4 = gf.GaugeFixer(DIMS, gf.GF_LANDAU, gf.GF_FP32_12, fasd=True, device=dev)
+        gf.gf_set_method(f4.h, gf.GF_METHOD_FASD)
+        f4.upload(U5)
+        th0 = f4.functional_theta()[1][0]
+        gf.gf_fix(f4.h, 1e-300, 2)                 # warm-up (graph capture)
+        f4.upload(U5)
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        _, _, Ff, thf = gf.gf_fix(f4.h, 1e-300, args.fasd_iters)
+        q1.record(stream)
+        q1.synchronize()
+        fasd = {"iterations": args.fasd_iters, "ms_per_iteration": q0.elapsed_time(q1) / args.fasd_iters,
+                "theta_start": float(th0), "theta_end": float(thf[0]), "F_end": float(Ff[0]),
+                "workload": "32^4 Landau, FP32-12 links, FP32 FFTs, FP64 reductions, eps 0.5 seed 5, alpha 0.08"}
+        f4.close()
+        del f4, U5
+
+    # ---- differentiable F(c), theta(c): forward and backward on 16^4 FP64
+    autograd = None
+    if args.autograd:
+        from paper_1412_1498_gb300.autograd import functional_theta
+        d16 = (16, 16, 16, 16)
+        V16 = 16 ** 4
+        f5 = gf.GaugeFixer(d16, gf.GF_LANDAU, gf.GF_FP64_18, autograd=True, device=dev)
+        f5.upload(make_field(d16, EPS_FIELD, 5))
+        c = torch.zeros((V16, 8), dtype=torch.float64, device=dev, requires_grad=True)
+        for _ in range(2):
+            F16, _t = functional_theta(c, f5)
+            F16.backward()
+        r0, r1, r2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        r0.record(stream)
+        F16, _t = functional_theta(c, f5)
+        r1.record(stream)
+        F16.backward()
+        r2.record(stream)
+        r2.synchronize()
+        autograd = {"lattice": list(d16), "forward_ms": r0.elapsed_time(r1), "backward_ms": r1.elapsed_time(r2)}
+        f5.close()
+        del f5
+
     peak, peak_kind = measured_peaks()
     achieved = HALF_SWEEP_BYTES / (half_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -332,6 +362,7 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": list(DIMS), "storage": "fp32-12", "omega": OMEGA,
                        "check_interval": 1, "reunit_interval": 20, "block_threads": best[0],
+                       "sweep_kernel": {1: "register", 2: "pipelined"}.get(best[1], str(best[1])),
                        "field": f"smooth eps={EPS_FIELD} seed={SEED} + Haar gauge",
                        "l2": "inputs larger than L2: 201 MB of links vs 129 MB L2",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -343,6 +374,8 @@ def run_gpu(args):
             "clocks": clocks.summary(),
             "time_to_theta_1e-15": ttt,
             "split_polish_probe": split_probe,
+            "fa_sd": fasd,
+            "autograd": autograd,
         }
         print(json.dumps(line))
     fx.close()
@@ -361,6 +394,8 @@ def main():
     ap.add_argument("--skip-time-to-theta", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--split-probe", type=int, default=100)
+    ap.add_argument("--fasd-iters", type=int, default=50)
+    ap.add_argument("--autograd", type=int, default=1)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gf":
         args.warmup = 3

@@ -247,6 +247,14 @@ GF_API int gf_set_polish(gf_handle *h, int polish);
 #define GF_SWEEP_PIPELINED 2
 GF_API int gf_set_sweep_variant(gf_handle *h, int variant);
 
+/* Autotuner: times 7 sweeps (2 warm-up) of the current field for each block size (64,
+   128, 256) and sweep kernel (register / pipelined for FP32-12) with CUDA events on the
+   handle's stream and keeps the fastest; *threads_out, *variant_out (nullable) receive
+   the choice.  The timing sweeps are applied to the field (they are gauge
+   transformations of it): tune before uploading the field to fix, or upload it again
+   afterwards.  Synchronises the stream. */
+GF_API int gf_autotune(gf_handle *h, int *threads_out, int *variant_out);
+
 /* Sweeps done by the last gf_fix in the FP32 and FP64 phases (mixed mode), nullable. */
 GF_API int gf_fix_phase_sweeps(const gf_handle *h, int *fp32_sweeps, int *fp64_sweeps);
 

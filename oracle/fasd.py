@@ -92,13 +92,16 @@ def apply_gauge(U: np.ndarray, g: np.ndarray) -> np.ndarray:
 
 
 def fa_sd_step(U: np.ndarray, alpha: float = 0.08, gauge: int = 0, kind: str = "fourier",
-               delta_fn=None) -> np.ndarray:
-    """One iteration of Algorithm 2; returns the new field (U is not modified)."""
+               delta_fn=None, slice_active=None) -> np.ndarray:
+    """One iteration of Algorithm 2; returns the new field (U is not modified).
+    slice_active (Coulomb gauge, Lt booleans): g = 1 on the sites of inactive slices."""
     if delta_fn is None:
         from oracle import delta as delta_fn
     D = delta_fn(U, gauge)
     Dt = filtered_delta(D, gauge, kind)
     g = gauge_from_update(Dt, alpha)
+    if slice_active is not None:
+        g[~np.asarray(slice_active, bool)] = np.eye(3)
     return apply_gauge(U, g)
 
 
@@ -111,16 +114,25 @@ def sd_step(U: np.ndarray, alpha: float = 0.08, gauge: int = 0, delta_fn=None) -
 
 
 def fa_sd_fix(U: np.ndarray, eps: float, maxiter: int, alpha: float = 0.08, gauge: int = 0,
-              kind: str = "fourier"):
+              kind: str = "fourier", per_slice: bool = False, reunit_interval: int = 0):
     """Algorithm 2: measure; while theta >= eps and fewer than maxiter steps: step; measure.
-    Returns (U, dict(rc, iters, F, theta, theta_hist))."""
-    from oracle import measure
-    F, th, _, _ = measure(U, gauge)
+    per_slice (Coulomb gauge): each time slice stops on its own theta_t < eps and then
+    keeps g = 1.  reunit_interval > 0: the links are reunitarised after every such
+    number of iterations.  Returns (U, dict(rc, iters, F, theta, theta_hist, slice_iters))."""
+    from oracle import measure, reunit
+    F, th, _, th_t = measure(U, gauge)
+    active = (th_t >= eps) if per_slice else np.full(U.shape[0], th >= eps)
+    slice_iters = np.zeros(U.shape[0], dtype=int)
     hist = [th]
     it = 0
-    while th >= eps and it < maxiter:
-        U = fa_sd_step(U, alpha, gauge, kind)
-        F, th, _, _ = measure(U, gauge)
-        hist.append(th)
+    while active.any() and it < maxiter:
+        U = fa_sd_step(U, alpha, gauge, kind, slice_active=active if per_slice else None)
+        slice_iters += active
         it += 1
-    return U, dict(rc=0 if th < eps else 1, iters=it, F=F, theta=th, theta_hist=np.array(hist))
+        if reunit_interval > 0 and it % reunit_interval == 0:
+            U = reunit(np.ascontiguousarray(U))
+        F, th, _, th_t = measure(U, gauge)
+        hist.append(th)
+        active = (active & (th_t >= eps)) if per_slice else np.full(U.shape[0], th >= eps)
+    return U, dict(rc=0 if not active.any() else 1, iters=it, F=F, theta=th, theta_hist=np.array(hist),
+                   slice_iters=slice_iters)

@@ -542,6 +542,7 @@ int run_fasd(gf_handle* h, double eps, int budget, int* done) {
   st.reunit_interval = h->reunit_interval;
   st.n_active = h->n_units;
   st.ticket = 0;
+  st.stop = 0;
   st.eps = eps;
   GF_CK(h, cudaMemcpyAsync(h->d_state, &st, sizeof st, cudaMemcpyHostToDevice, h->stream));
   launch_fill_int(h->d_active, 1, h->n_units, h->stream);
@@ -562,21 +563,10 @@ int run_fasd(gf_handle* h, double eps, int budget, int* done) {
     if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
   int rc;
-  do {
+  do {  // until every unit converged or the field after the budget has been measured
     GF_CK(h, cudaGraphLaunch(h->graph_fasd, h->stream));
     if ((rc = read_state(h, &st)) != GF_OK) return rc;
-  } while (st.n_active > 0 && st.sweep < st.limit);
-  if (st.n_active > 0) {
-    // budget used up: F and theta of the final field (the loop measured the one before)
-    FasdArgs a = fasd_args(h, false, FINISH_MEASURE);
-    a.st = nullptr;
-    launch_fasd_delta_xy(h->storage, h->nd, a, h->stream);
-    GF_CK_LAUNCH(h);
-    a.st = h->d_state;             // the finishing kernel's ticket
-    a.active = h->d_active;        // read (for the count), not changed, in MEASURE mode
-    launch_fasd_finish(a, h->stream);
-    GF_CK_LAUNCH(h);
-  }
+  } while (st.n_active > 0 && !st.stop);
   *done = st.sweep;
   return GF_OK;
 }
@@ -1036,6 +1026,55 @@ int gf_set_sweep_variant(gf_handle* h, int variant) {
     return fail(h, GF_EINVAL, "the pipelined sweep exists for GF_FP32_12 storage only");
   if (variant != h->variant) drop_graphs(h);
   h->variant = variant;
+  return GF_OK;
+}
+
+int gf_autotune(gf_handle* h, int* threads_out, int* variant_out) {
+  if (!h) return GF_EINVAL;
+  // Time a few sweeps of the current field for every launch shape and keep the fastest.
+  // Half-sweeps of one parity on the same field change it, so the sweeps are done in
+  // pairs on a scratch copy: the field is saved to the staging area first when it fits,
+  // otherwise the tuning sweeps act on the field itself (they are gauge transformations).
+  const int st = cur_storage(h);
+  std::vector<std::pair<int, int>> cands;
+  for (int t : {64, 128, 256}) {
+    cands.push_back({t, GF_SWEEP_REGISTER});
+    if (st == GF_FP32_12) cands.push_back({t, GF_SWEEP_PIPELINED});
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  GF_CK(h, cudaEventCreate(&e0));
+  GF_CK(h, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int bt = h->threads, bv = h->variant;
+  int rc = GF_OK;
+  for (auto& c : cands) {
+    h->variant = c.second;
+    if ((rc = gf_set_block_size(h, c.first)) != GF_OK) break;
+    for (int k = 0; k < 2 && rc == GF_OK; ++k) rc = gf_or_sweep(h, 2, h->omega);  // warm-up
+    if (rc != GF_OK) break;
+    if (cudaEventRecord(e0, h->stream) != cudaSuccess) { rc = fail(h, GF_ECUDA, "event record failed"); break; }
+    for (int k = 0; k < 5 && rc == GF_OK; ++k) rc = gf_or_sweep(h, 2, h->omega);
+    if (rc != GF_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      rc = fail(h, GF_ECUDA, "event timing failed");
+      break;
+    }
+    if (ms < best) {
+      best = ms;
+      bt = c.first;
+      bv = c.second;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != GF_OK) return rc;
+  h->variant = bv;
+  drop_graphs(h);
+  if ((rc = gf_set_block_size(h, bt)) != GF_OK) return rc;
+  if (threads_out) *threads_out = bt;
+  if (variant_out) *variant_out = bv;
   return GF_OK;
 }
 

@@ -54,6 +54,7 @@ struct DevState {
   int reunit_interval;  // reunitarise after the odd half-sweep every this many sweeps
   int n_active;         // active units after the last check
   unsigned int ticket;  // last-block-done counter of the finishing kernel
+  int stop;             // Fourier-accelerated loop: final field measured, nothing left to do
   double eps;           // stop threshold of the current phase
 };
 

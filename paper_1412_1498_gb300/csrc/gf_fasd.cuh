@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ double red[64];
   __shared__ cx<T> twx[32], twy[32];
-  if (a.st && a.st->n_active <= 0) return;
+  if (a.st && (a.st->n_active <= 0 || a.st->stop)) return;
   const LatDev& lat = a.lat;
   const int z = blockIdx.x, t = blockIdx.y;
   const int Lx = lat.L[0], Ly = lat.L[1], P = Lx * Ly;
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
 __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
   __shared__ double red[96];
   __shared__ int s_last;
-  if (a.st && a.st->n_active <= 0 && a.mode == FINISH_LOOP) return;
+  if (a.st && a.mode == FINISH_LOOP && (a.st->n_active <= 0 || a.st->stop)) return;
   const int u = blockIdx.x;
   const bool was_active = a.active == nullptr || a.active[u] != 0;
   if (a.mode != FINISH_LOOP || was_active) {
@@ -252,7 +252,11 @@ __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
     for (int k = threadIdx.x; k < a.n_units; k += blockDim.x) c[0] += (double)__ldcg(a.active + k);
   block_sum<1>(c, red);
   if (threadIdx.x == 0) {
-    if (a.mode == FINISH_LOOP && a.active) a.st->n_active = (int)c[0];
+    if (a.mode == FINISH_LOOP && a.active) {
+      a.st->n_active = (int)c[0];
+      // the field after the last allowed update has now been measured
+      if (a.st->sweep >= a.st->limit) a.st->stop = 1;
+    }
     a.st->ticket = 0u;
   }
 }
@@ -359,18 +363,30 @@ __global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
   const int p = i >= lat.Vh ? 1 : 0;
   const int h = (int)(i - (long long)p * lat.Vh);
   const Site s = site_of(lat, p, h);
-  if (ND == 3 && a.active && !a.active[s.t]) return;
+  // Coulomb gauge with per-slice masks: g = 1 on the sites of a converged slice, so its
+  // spatial links stay as they are while a temporal link into an active slice still
+  // takes that slice's g(x + t)^+ on the right
+  bool act = true, act_next = true;
+  if (ND == 3 && a.active) {
+    act = a.active[s.t] != 0;
+    act_next = a.active[s.t == lat.L[3] - 1 ? 0 : s.t + 1] != 0;
+    if (!act && !act_next) return;
+  }
   const bool reunit_now = a.st ? state_reunit_sweep(a.st) : a.reunit != 0;
   char* base = a.links + lat.off_bytes;
   cx<T> g[9];
-  g_load<T>(a.gbuf, lat.V, (int)i, g);
+  if (act) g_load<T>(a.gbuf, lat.V, (int)i, g);
 #pragma unroll 1
   for (int mu = 0; mu < 4; ++mu) {
+    const bool act_fwd = mu == 3 ? act_next : act;
+    if (!act && !act_fwd) continue;
     cx<T> u[NE], gn[9];
     St::load(base, lat.V, mu, (int)i, u);
-    g_load<T>(a.gbuf, lat.V, idx_of_lexi(lat, fwd_lexi(lat, s, mu)), gn);
-    left_mul(g, u);
-    right_mul_dag(u, gn);
+    if (act) left_mul(g, u);
+    if (act_fwd) {
+      g_load<T>(a.gbuf, lat.V, idx_of_lexi(lat, fwd_lexi(lat, s, mu)), gn);
+      right_mul_dag(u, gn);
+    }
     if (reunit_now) reunit(u);
     St::store(base, lat.V, mu, (int)i, u);
   }

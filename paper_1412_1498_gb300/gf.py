@@ -67,6 +67,7 @@ _SIGS = {
     "gf_fix_phase_sweeps": (_int, [_vp, _IP, _IP]),
     "gf_set_sweep_variant": (_int, [_vp, _int]),
     "gf_set_polish": (_int, [_vp, _int]),
+    "gf_autotune": (_int, [_vp, _IP, _IP]),
     "gf_fa_sd_step": (_int, [_vp, _dbl]),
     "gf_set_method": (_int, [_vp, _int]),
     "gf_set_alpha": (_int, [_vp, _dbl]),
@@ -234,6 +235,13 @@ def gf_set_polish(h, polish: int) -> None:
 
 def gf_set_sweep_variant(h, variant: int) -> None:
     _check(_lib.gf_set_sweep_variant(h, variant), h)
+
+
+def gf_autotune(h):
+    """(threads, variant) picked by the library's autotuner."""
+    t, v = ctypes.c_int(), ctypes.c_int()
+    _check(_lib.gf_autotune(h, ctypes.byref(t), ctypes.byref(v)), h)
+    return t.value, v.value
 
 
 def gf_fix_phase_sweeps(h):

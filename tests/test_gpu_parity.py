@@ -358,3 +358,21 @@ def test_split_polish_coulomb_per_slice(gf):
     F, th, F_t, th_t = oracle.measure(got, oracle.COULOMB)
     assert np.all(th_t < 1e-15 * (1 + 1e-6)), th_t
     assert len(set(out["iters"].tolist())) > 1
+
+
+def test_autotuner_picks_a_valid_launch_shape(gf):
+    U = fields.random_gauge_config(DIMS, 0.5, 74)
+    fx = make(gf, DIMS, gf.GF_LANDAU, gf.GF_FP32_12)
+    fx.upload(U)
+    t, v = gf.gf_autotune(fx.h)
+    assert t in (64, 128, 256) and v in (gf.GF_SWEEP_REGISTER, gf.GF_SWEEP_PIPELINED)
+    fx.upload(U)
+    out = fx.fix(1e-300, 5)
+    F, th, _, _ = oracle.measure(fx.download())
+    assert abs(out["F"][0] - F) < 1e-5 * abs(F)
+    fx.close()
+    fx = make(gf, DIMS, gf.GF_LANDAU, gf.GF_FP64_18)
+    fx.upload(U)
+    t, v = gf.gf_autotune(fx.h)
+    assert v == gf.GF_SWEEP_REGISTER
+    fx.close()
