@@ -42,6 +42,25 @@ HALF_SWEEP_BYTES = 8 * V * LINK_B
 WORKLOAD = "landau-32^4-fp32-12: OR sweep (even+odd, omega 1.7, reunit every 20) + F/theta"
 
 
+def profiled_traffic(profile: str, sources) -> int | None:
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's sources still
+    hash to the value recorded there (otherwise the counters describe another kernel)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", profile)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_hash = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    m_bytes = re.search(r"dram_bytes_per_launch:\s*(\d+)", text)
+    if not m_hash or not m_bytes:
+        return None
+    h = hashlib.sha256()
+    for src in sources:
+        h.update(open(os.path.join(ROOT, "paper_1412_1498_gb300", "csrc", src), "rb").read())
+    return int(m_bytes.group(1)) if h.hexdigest() == m_hash.group(1) else None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -340,8 +359,14 @@ def run_gpu(args):
 
     peak, peak_kind = measured_peaks()
     achieved = HALF_SWEEP_BYTES / (half_ms * 1e-3) / 1e9
+    traffic = None
+    if best[1] == gf.GF_SWEEP_PIPELINED:
+        traffic = profiled_traffic("k_or_sweep_pipe_fp32_12_landau_32x4.md",
+                                   ("gf_device.cuh", "gf_kernels.cuh", "gf_sweep_pipe.cuh"))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_or_sweep<FP32_12, Landau>",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_or_sweep_pipe<Landau> (FP32-12)" if best[1] == gf.GF_SWEEP_PIPELINED
+                else "k_or_sweep<FP32_12, Landau>",
                 "bytes_per_launch": HALF_SWEEP_BYTES, "ms_per_launch": half_ms,
                 "peak_kind": f"{peak_kind} HBM copy bandwidth"}
 

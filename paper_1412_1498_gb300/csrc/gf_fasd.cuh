@@ -27,17 +27,23 @@ namespace gf {
 // In-place radix-2 FFTs of n_lines lines of length L = 2^logL in shared memory; line l
 // starts at d[(l % n_in) * in_stride + (l / n_in) * out_stride], its element k sits
 // estride further per k.  sign = -1 forward, +1 inverse (no 1/L).  tw[k] = exp(-2 pi i
-// k / L), k < L/2.  Contains __syncthreads(): call from every thread of the block.
+// k / L), k < L/2.  n_lines and n_in are powers of 2.  Lines with contiguous elements
+// (estride 1) are walked butterfly-fastest; strided lines line-fastest, so that the
+// threads of a warp touch consecutive words (no shared-memory bank conflicts beyond the
+// two wavefronts of 64-bit accesses).  Contains __syncthreads(): call from all threads.
 template <class T>
 __device__ __forceinline__ void fft_lines(cx<T>* d, const cx<T>* tw, int n_lines, int logL, int n_in,
                                           int in_stride, int out_stride, int estride, int sign) {
   const int L = 1 << logL;
-  const int tot = n_lines * L;
+  const int ll = __ffs(n_lines) - 1, li = __ffs(n_in) - 1;
+  const bool lf = estride != 1;
+  const int tot = n_lines << logL;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int l = i >> logL, k = i & (L - 1);
+    const int l = lf ? (i & (n_lines - 1)) : (i >> logL);
+    const int k = lf ? (i >> ll) : (i & (L - 1));
     const int r = logL ? (int)(__brev((unsigned)k) >> (32 - logL)) : 0;
     if (k < r) {
-      const int o = (l % n_in) * in_stride + (l / n_in) * out_stride;
+      const int o = (l & (n_in - 1)) * in_stride + (l >> li) * out_stride;
       cx<T>* a = d + o + k * estride;
       cx<T>* b = d + o + r * estride;
       const cx<T> t = *a;
@@ -50,11 +56,12 @@ __device__ __forceinline__ void fft_lines(cx<T>* d, const cx<T>* tw, int n_lines
   for (int s = 1; s <= logL; ++s) {
     const int half = 1 << (s - 1);
     for (int i = threadIdx.x; i < hb; i += blockDim.x) {
-      const int l = i >> (logL - 1), b = i & ((L >> 1) - 1);
+      const int l = lf ? (i & (n_lines - 1)) : (i >> (logL - 1));
+      const int b = lf ? (i >> ll) : (i & ((L >> 1) - 1));
       const int j = b & (half - 1), k0 = ((b >> (s - 1)) << s) + j, k1 = k0 + half;
       cx<T> w = tw[j << (logL - s)];
       if (sign > 0) w.im = -w.im;
-      const int o = (l % n_in) * in_stride + (l / n_in) * out_stride;
+      const int o = (l & (n_in - 1)) * in_stride + (l >> li) * out_stride;
       cx<T>* p0 = d + o + k0 * estride;
       cx<T>* p1 = d + o + k1 * estride;
       const cx<T> u = *p0, v = cmul(*p1, w);
@@ -200,6 +207,7 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
   fft_lines(pl, twy, 4 * Lx, a.logL[1], Lx, 1, P, Lx, -1);       // columns (f, x), along y
   cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf);
   const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
+#pragma unroll 8
   for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
     const int f = i / P, j = i % P;
     kb[f * lat.V + plane0 + j] = pl[i];
@@ -262,53 +270,70 @@ __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
 }
 
 // ------------------------------------------------------------------------- C: FFT z(t), filter
-// Block: one ky, KX consecutive kx, and (Coulomb) one t; loops over the four fields.
+// Block: one field, one ky, KX consecutive kx and (Coulomb) one t.  Shared layout
+// col[kxl + KX z + (KX Lz + 4) tl]: the pad keeps both transform directions free of bank
+// conflicts.
 template <class T, int ND>
 __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ cx<T> twz[32], twt[32];
+  __shared__ T s2z[64], s2t[64];   // 4 sin^2(pi k / L) along z and t
   if (!fasd_running(a.st)) return;
   const LatDev& lat = a.lat;
   const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2], Lt = lat.L[3];
-  const int KX = Lx < 4 ? Lx : 4;
+  const int lz = a.logL[2];
+  const int KX = Lx < 4 ? Lx : 4, lk = KX == 4 ? 2 : (KX == 2 ? 1 : 0);
   const int kx0 = blockIdx.x * KX, ky = blockIdx.y;
-  const int t0 = ND == 4 ? 0 : (int)blockIdx.z, nt = ND == 4 ? Lt : 1;
+  const int f = ND == 4 ? (int)blockIdx.z : (int)blockIdx.z & 3;
+  const int t0 = ND == 4 ? 0 : (int)blockIdx.z >> 2, nt = ND == 4 ? Lt : 1;
   if (ND == 3 && a.active && !a.active[t0]) return;
-  cx<T>* col = reinterpret_cast<cx<T>*>(smraw);  // [nt][Lz][KX]
-  twiddles(twz, a.logL[2]);
+  cx<T>* col = reinterpret_cast<cx<T>*>(smraw);
+  const int pitch = KX * Lz + 4;
+  twiddles(twz, lz);
   if (ND == 4) twiddles(twt, a.logL[3]);
+  for (int k = threadIdx.x; k < Lz; k += blockDim.x) {
+    const T sn = sinpi((T)k / (T)Lz);
+    s2z[k] = T(4) * sn * sn;
+  }
+  if (ND == 4)
+    for (int k = threadIdx.x; k < Lt; k += blockDim.x) {
+      const T sn = sinpi((T)k / (T)Lt);
+      s2t[k] = T(4) * sn * sn;
+    }
+  T p2xy[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const T sx = sinpi((T)(kx0 + (j < KX ? j : 0)) / (T)Lx), sy = sinpi((T)ky / (T)Ly);
+    p2xy[j] = T(4) * sx * sx + T(4) * sy * sy;
+  }
   __syncthreads();
-  cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf);
+  cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf) + f * lat.V;
   const long long P = (long long)Lx * Ly;
-  const int n = nt * Lz * KX;
-  for (int f = 0; f < 4; ++f) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int kxl = i % KX, z = (i / KX) % Lz, tl = i / (KX * Lz);
-      col[i] = kb[f * lat.V + P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl];
-    }
-    __syncthreads();
-    // col[kxl + KX (z + Lz tl)]: along z the lines are (kxl, tl), along t they are (kxl, z)
-    fft_lines(col, twz, nt * KX, a.logL[2], KX, 1, Lz * KX, KX, -1);
-    if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, Lz * KX, -1);
-    // filter
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int kxl = i % KX, kz = (i / KX) % Lz, kt = i / (KX * Lz);
-      T p2 = T(0), sn;
-      sn = sinpi((T)(kx0 + kxl) / (T)Lx); p2 += T(4) * sn * sn;
-      sn = sinpi((T)ky / (T)Ly);          p2 += T(4) * sn * sn;
-      sn = sinpi((T)kz / (T)Lz);          p2 += T(4) * sn * sn;
-      if (ND == 4) { sn = sinpi((T)kt / (T)Lt); p2 += T(4) * sn * sn; }
-      const T fac = p2 > T(0) ? (T)a.coef / p2 : T(0);
-      col[i] = cscale(col[i], fac);
-    }
-    __syncthreads();
-    if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, Lz * KX, +1);
-    fft_lines(col, twz, nt * KX, a.logL[2], KX, 1, Lz * KX, KX, +1);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int kxl = i % KX, z = (i / KX) % Lz, tl = i / (KX * Lz);
-      kb[f * lat.V + P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl] = col[i];
-    }
-    __syncthreads();
+  const int n = nt << (lz + lk);
+  const int mz = Lz - 1, mk = KX - 1;
+#pragma unroll 8
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);
+    col[kxl + KX * z + pitch * tl] = kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl];
+  }
+  __syncthreads();
+  fft_lines(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);          // along z
+  if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, -1);  // along t
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int kxl = i & mk, kz = (i >> lk) & mz, kt = i >> (lk + lz);
+    T p2 = p2xy[kxl] + s2z[kz];
+    if (ND == 4) p2 += s2t[kt];
+    const T fac = p2 > T(0) ? (T)a.coef / p2 : T(0);
+    const int c = kxl + KX * kz + pitch * kt;
+    col[c] = cscale(col[c], fac);
+  }
+  __syncthreads();
+  if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, +1);
+  fft_lines(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
+#pragma unroll 8
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);
+    kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl] = col[kxl + KX * z + pitch * tl];
   }
 }
 
@@ -329,6 +354,7 @@ __global__ void __launch_bounds__(256) k_fasd_xy_inv_g(FasdArgs a) {
   twiddles(twy, a.logL[1]);
   const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf);
   const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
+#pragma unroll 8
   for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) pl[i] = kb[(i / P) * lat.V + plane0 + i % P];
   __syncthreads();
   fft_lines(pl, twy, 4 * Lx, a.logL[1], Lx, 1, P, Lx, +1);

@@ -10,7 +10,7 @@ static size_t plane_smem(int storage, const LatDev& lat) {
 static size_t column_smem(int storage, int nd, const LatDev& lat) {
   const size_t c = storage == GF_FP64_18 ? 16 : 8;
   const int KX = lat.L[0] < 4 ? lat.L[0] : 4;
-  return (size_t)(nd == 4 ? lat.L[3] : 1) * lat.L[2] * KX * c;
+  return (size_t)(nd == 4 ? lat.L[3] : 1) * (lat.L[2] * KX + 4) * c;
 }
 
 // Shared-memory opt-in for every FA-SD kernel (outside any stream capture).
@@ -48,7 +48,7 @@ void launch_fasd_finish(const FasdArgs& a, cudaStream_t s) { k_fasd_finish<<<a.n
 
 void launch_fasd_zt(int storage, int nd, const FasdArgs& a, cudaStream_t s) {
   const int KX = a.lat.L[0] < 4 ? a.lat.L[0] : 4;
-  const dim3 grid(a.lat.L[0] / KX, a.lat.L[1], nd == 4 ? 1 : a.lat.L[3]);
+  const dim3 grid(a.lat.L[0] / KX, a.lat.L[1], nd == 4 ? 4 : 4 * a.lat.L[3]);
   const size_t sm = column_smem(storage, nd, a.lat);
 #define GF_CALL(S, T, ND) k_fasd_zt<T, ND><<<grid, 256, sm, s>>>(a)
   GF_FASD_SWITCH(storage, nd, GF_CALL)
