@@ -61,6 +61,17 @@ def profiled_traffic(profile: str, sources) -> int | None:
     return int(m_bytes.group(1)) if h.hexdigest() == m_hash.group(1) else None
 
 
+def reduce_over_ranks(ms_total: float, steps: int, world: int, bytes_per_step: int, dist=None, device=None):
+    """Whole-job throughput of a weak-scaling run: every rank processed its own lattice;
+    the slowest rank's time counts.  Returns (max ms over ranks, GB/s of all ranks)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([ms_total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    return ms_total, world * bytes_per_step * steps / (ms_total * 1e-3) / 1e9
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -249,9 +260,8 @@ def run_gpu(args):
         k1.synchronize()
         half_ms = k0.elapsed_time(k1) / n_half
     assert int(iters[0]) == args.steps, (iters, args.steps)
-    ms_total = max_over_ranks(ms_total)
+    ms_total, value = reduce_over_ranks(ms_total, args.steps, world, STEP_BYTES, dist, dev)
     ms_step = ms_total / args.steps
-    value = world * STEP_BYTES * args.steps / (ms_total * 1e-3) / 1e9
     graph_sweeps = 16
     launches = 3 + ((args.steps + graph_sweeps - 1) // graph_sweeps) * graph_sweeps * 4
 

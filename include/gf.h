@@ -130,7 +130,8 @@ GF_API int gf_num_units(const gf_handle *h);
  *   links: canonical layout, 2*9*4*V float64; on_device = 1 if it is device memory,
  *   0 if host memory (pinned memory gives the fastest copies).
  *   Upload rounds to the handle's storage (FP32 and/or 12 reals: row 2 is dropped) and
- *   resets the sweep counter, the masks (all units active) and the iteration counts.
+ *   resets the sweep count (gf_get_sweeps_done), the masks (all units active) and the
+ *   iteration counts.
  *   Download reconstructs row 2 in FP64 for 12-real storage.  In mixed mode gf_fix
  *   leaves the field in the FP64 copy and download reads that copy; an upload moves
  *   the handle back to its primary storage, so upload every lattice of a batch before
@@ -167,8 +168,8 @@ GF_API int gf_reunitarize(gf_handle *h);
  * Algorithm 1: measure; while a unit has theta >= eps and fewer than maxiter sweeps
  * were done: even half-sweep, odd half-sweep (reunitarising the links it writes after
  * every reunit_interval-th sweep), then F and theta every check_interval sweeps; a
- * unit whose theta < eps is masked and no longer updated.  The sweep counter for the
- * reunitarisation schedule starts at 0 in each call.
+ * unit whose theta < eps is masked and no longer updated.  The schedule counts sweeps
+ * from the last upload (see gf_get_sweeps_done).
  *   eps > 0; maxiter >= 0.  iters (nullable): gf_num_units ints, sweeps each unit
  *   received.  F, theta (nullable): n_lat final values.
  *   With GF_FLAG_MIXED: FP32 sweeps until every unit has theta < the switch threshold
@@ -254,6 +255,16 @@ GF_API int gf_set_sweep_variant(gf_handle *h, int variant);
    transformations of it): tune before uploading the field to fix, or upload it again
    afterwards.  Synchronises the stream. */
 GF_API int gf_autotune(gf_handle *h, int *threads_out, int *variant_out);
+
+/* Checkpoint / resume.  The handle counts the sweeps (or Fourier-accelerated iterations)
+   done since the last upload; the reunitarisation and check schedule of gf_fix continues
+   from that count (the sweep after n sweeps is sweep n + 1).  To resume a run: download
+   the links, read the count, later upload the links into a handle with the same settings
+   and set the count; the continued run gives the bits of the uninterrupted one (FP64-18,
+   or any storage in non-mixed mode).  Mixed-precision gf_fix restarts the count in each
+   precision phase.  Upload resets it to 0. */
+GF_API int gf_get_sweeps_done(const gf_handle *h, int *n);
+GF_API int gf_set_sweeps_done(gf_handle *h, int n);
 
 /* Sweeps done by the last gf_fix in the FP32 and FP64 phases (mixed mode), nullable. */
 GF_API int gf_fix_phase_sweeps(const gf_handle *h, int *fp32_sweeps, int *fp64_sweeps);

@@ -263,6 +263,7 @@ struct gf_handle {
   int cur = 0;  // 0: primary buffer holds the field, 1: polish buffer in FP64-18,
                 // 2: polish buffer in double-float (only inside gf_fix)
   int phase_sweeps[2] = {0, 0};
+  int sweeps_done = 0;  // since the last upload: the reunitarisation / check schedule
   // graphs: one per buffer state (OR), one for Fourier acceleration
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
   cudaGraphExec_t graph_fasd = nullptr;
@@ -451,8 +452,9 @@ int read_state(gf_handle* h, DevState* out) {
 // unit is below eps or `budget` sweeps were done.  *done receives the sweeps done.
 int run_phase(gf_handle* h, double eps, int budget, int* done) {
   DevState s{};
-  s.sweep = 0;
-  s.limit = budget;
+  const int offset = h->sweeps_done;
+  s.sweep = offset;
+  s.limit = offset + budget;
   s.check_interval = h->check_interval;
   s.reunit_interval = h->reunit_interval;
   s.n_active = 0;
@@ -467,7 +469,7 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
     GF_CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
   }
-  *done = s.sweep;
+  *done = s.sweep - offset;
   return GF_OK;
 }
 
@@ -536,8 +538,9 @@ int enqueue_fasd_iteration(gf_handle* h, cudaStream_t s) {
 
 int run_fasd(gf_handle* h, double eps, int budget, int* done) {
   DevState st{};
-  st.sweep = 0;
-  st.limit = budget;
+  const int offset = h->sweeps_done;
+  st.sweep = offset;
+  st.limit = offset + budget;
   st.check_interval = 1;
   st.reunit_interval = h->reunit_interval;
   st.n_active = h->n_units;
@@ -567,7 +570,7 @@ int run_fasd(gf_handle* h, double eps, int budget, int* done) {
     GF_CK(h, cudaGraphLaunch(h->graph_fasd, h->stream));
     if ((rc = read_state(h, &st)) != GF_OK) return rc;
   } while (st.n_active > 0 && !st.stop);
-  *done = st.sweep;
+  *done = st.sweep - offset;
   return GF_OK;
 }
 
@@ -750,6 +753,7 @@ int gf_upload(gf_handle* h, int lat, const double* links, int on_device) {
   if (lat < 0 || lat >= h->n_lat || !links) return fail(h, GF_EINVAL, "bad lattice index or null buffer");
   if (on_device && ((uintptr_t)links % 16) != 0) return fail(h, GF_EINVAL, "device buffer must be 16-byte aligned");
   h->cur = 0;
+  h->sweeps_done = 0;
   const LatDev& d = h->lats[lat];
   if (on_device) {
     launch_pack(h->storage, h->links, d, links, 0, d.V, h->stream);
@@ -835,6 +839,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
     if (!(h->flags & GF_FLAG_FASD)) return fail(h, GF_ESTATE, "create the handle with GF_FLAG_FASD for Fourier acceleration");
     if (h->cur != 0) return fail(h, GF_ESTATE, "upload the field before a Fourier-accelerated fix");
     if ((rc = run_fasd(h, eps, maxiter, &done)) != GF_OK) return rc;
+    h->sweeps_done += done;
     h->phase_sweeps[h->storage == GF_FP64_18 ? 1 : 0] = done;
     if ((rc = copy_out(h, F, theta, nullptr, nullptr, iters)) != GF_OK) return rc;
     DevState s{};
@@ -843,6 +848,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
   }
   const bool mixed = (h->flags & GF_FLAG_MIXED) && h->cur == 0;
   if (mixed) {
+    h->sweeps_done = 0;  // each precision phase keeps its own schedule
     if ((rc = run_phase(h, std::max(eps, h->eps_switch), maxiter, &done)) != GF_OK) return rc;
     h->phase_sweeps[0] = done;
     int done2 = 0;
@@ -853,6 +859,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
         GF_CK_LAUNCH(h);
       }
       h->cur = 2;
+      h->sweeps_done = 0;
       rc = run_phase(h, eps, maxiter - done, &done2);
       for (int l = 0; l < h->n_lat; ++l) {
         launch_split_to_fp64(h->links64, h->lats64[l], h->stream);
@@ -869,10 +876,13 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
       h->cur = 1;
     }
     int done3 = 0;
+    h->sweeps_done = 0;
     if ((rc = run_phase(h, eps, maxiter - done, &done3)) != GF_OK) return rc;
+    h->sweeps_done = done3;
     h->phase_sweeps[1] = done2 + done3;
   } else {
     if ((rc = run_phase(h, eps, maxiter, &done)) != GF_OK) return rc;
+    h->sweeps_done += done;
     h->phase_sweeps[h->cur == 1 || h->storage == GF_FP64_18 ? 1 : 0] = done;
   }
   if ((rc = copy_out(h, F, theta, nullptr, nullptr, iters)) != GF_OK) return rc;
@@ -1075,6 +1085,19 @@ int gf_autotune(gf_handle* h, int* threads_out, int* variant_out) {
   if ((rc = gf_set_block_size(h, bt)) != GF_OK) return rc;
   if (threads_out) *threads_out = bt;
   if (variant_out) *variant_out = bv;
+  return GF_OK;
+}
+
+int gf_get_sweeps_done(const gf_handle* h, int* n) {
+  if (!h || !n) return GF_EINVAL;
+  *n = h->sweeps_done;
+  return GF_OK;
+}
+
+int gf_set_sweeps_done(gf_handle* h, int n) {
+  if (!h) return GF_EINVAL;
+  if (n < 0) return fail(h, GF_EINVAL, "sweep count must be >= 0");
+  h->sweeps_done = n;
   return GF_OK;
 }
 

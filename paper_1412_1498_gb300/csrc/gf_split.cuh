@@ -325,35 +325,39 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
     for (int e = 0; e < 18; ++e) A[e] = {0.f, 0.f};
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
-      csf f[9], b[9];
-      split_load(base, V, mu, idx_f, f);
-      split_load(base, V, mu, idx_b[mu], b);
-      cx<float> df[9], db[9];
+      // forward link: U_mu(x) += E U_mu(x); then backward: U_mu(x-mu) += U_mu(x-mu) E^+
+      // (one split link live at a time)
+#pragma unroll 1
+      for (int side = 0; side < 2; ++side) {
+        const int idx = side == 0 ? idx_f : idx_b[mu];
+        csf u[9];
+        split_load(base, V, mu, idx, u);
+        cx<float> du[9];
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
+        for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          cx<float> x = {0.f, 0.f}, y = {0.f, 0.f};
+          for (int c = 0; c < 3; ++c) {
+            cx<float> x = {0.f, 0.f};
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            x = cadd(x, cmul(E[3 * r + k], csf_hi(f[3 * k + c])));
-            y = cadd(y, cmul(csf_hi(b[3 * r + k]), cconj(E[3 * c + k])));
+            for (int k = 0; k < 3; ++k)
+              x = side == 0 ? cadd(x, cmul(E[3 * r + k], csf_hi(u[3 * k + c])))
+                            : cadd(x, cmul(csf_hi(u[3 * r + k]), cconj(E[3 * c + k])));
+            du[3 * r + c] = x;
           }
-          df[3 * r + c] = x;
-          db[3 * r + c] = y;
-        }
 #pragma unroll
-      for (int e = 0; e < 9; ++e) {
-        f[e] = csf_add_c(f[e], df[e]);
-        b[e] = csf_add_c(b[e], db[e]);
+        for (int e = 0; e < 9; ++e) u[e] = csf_add_c(u[e], du[e]);
+        if (reunit_now) split_reunit(u);
+        if (mu < ND && measure_now) {
+          // A += U_nu(x - nu) - U_nu(x)
+#pragma unroll
+          for (int e = 0; e < 9; ++e) {
+            const float sg = side == 0 ? -1.f : 1.f;
+            acc_add(A[2 * e], sg * u[e].re.hi, sg * u[e].re.lo);
+            acc_add(A[2 * e + 1], sg * u[e].im.hi, sg * u[e].im.lo);
+          }
+        }
+        split_store(base, V, mu, idx, u);
       }
-      if (reunit_now) {
-        split_reunit(f);
-        split_reunit(b);
-      }
-      if (mu < ND && measure_now) split_add_to_A(A, f, b);
-      split_store(base, V, mu, idx_f, f);
-      split_store(base, V, mu, idx_b[mu], b);
     }
     if (measure_now) q = split_theta_site(A);
   }

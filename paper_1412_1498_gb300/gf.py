@@ -68,6 +68,8 @@ _SIGS = {
     "gf_set_sweep_variant": (_int, [_vp, _int]),
     "gf_set_polish": (_int, [_vp, _int]),
     "gf_autotune": (_int, [_vp, _IP, _IP]),
+    "gf_get_sweeps_done": (_int, [_vp, _IP]),
+    "gf_set_sweeps_done": (_int, [_vp, _int]),
     "gf_fa_sd_step": (_int, [_vp, _dbl]),
     "gf_set_method": (_int, [_vp, _int]),
     "gf_set_alpha": (_int, [_vp, _dbl]),
@@ -242,6 +244,16 @@ def gf_autotune(h):
     t, v = ctypes.c_int(), ctypes.c_int()
     _check(_lib.gf_autotune(h, ctypes.byref(t), ctypes.byref(v)), h)
     return t.value, v.value
+
+
+def gf_get_sweeps_done(h) -> int:
+    n = ctypes.c_int()
+    _check(_lib.gf_get_sweeps_done(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def gf_set_sweeps_done(h, n: int) -> None:
+    _check(_lib.gf_set_sweeps_done(h, n), h)
 
 
 def gf_fix_phase_sweeps(h):

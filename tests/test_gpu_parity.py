@@ -376,3 +376,29 @@ def test_autotuner_picks_a_valid_launch_shape(gf):
     t, v = gf.gf_autotune(fx.h)
     assert v == gf.GF_SWEEP_REGISTER
     fx.close()
+
+
+@pytest.mark.parametrize("gauge", [0, 1])
+def test_checkpoint_resume_is_bit_exact(gf, gauge):
+    # 100 sweeps in one go == 57 sweeps, download, new handle, upload, count 57, 43 more
+    dims = DIMS if gauge == 0 else DIMS_C
+    U = fields.random_gauge_config(dims, 0.5, 75)
+    fa = make(gf, dims, gauge, gf.GF_FP64_18, repro=True)
+    fa.upload(U)
+    fa.fix(1e-300, 100)
+    assert gf.gf_get_sweeps_done(fa.h) == 100
+    whole = fa.download()
+    fa.close()
+    fb = make(gf, dims, gauge, gf.GF_FP64_18, repro=True)
+    fb.upload(U)
+    fb.fix(1e-300, 57)
+    ck, n = fb.download(), gf.gf_get_sweeps_done(fb.h)
+    fb.close()
+    assert n == 57
+    fc = make(gf, dims, gauge, gf.GF_FP64_18, repro=True)
+    fc.upload(ck)
+    assert gf.gf_get_sweeps_done(fc.h) == 0
+    gf.gf_set_sweeps_done(fc.h, n)
+    fc.fix(1e-300, 43)
+    assert np.array_equal(fc.download(), whole)
+    fc.close()
