@@ -62,14 +62,20 @@ extern "C" {
 #define GF_LANDAU 0
 #define GF_COULOMB 1
 
-/* link storage in device memory (Section 2: 18 or 12 real numbers per SU(3) link) */
+/* link storage in device memory (Section 2: 18, 12 or 8 real numbers per SU(3) link) */
 #define GF_FP64_18 0 /* full matrix, FP64 */
 #define GF_FP32_18 1 /* full matrix, FP32 */
 #define GF_FP32_12 2 /* rows 0 and 1, FP32; row 2 = conj(row0 x row1) on every load */
+#define GF_FP64_12 3 /* rows 0 and 1, FP64; row 2 rebuilt on every load */
+#define GF_FP32_8 4  /* u01, u02, u10, arg u00, arg u20 in FP32; rows 0 and 1 rebuilt from
+                        unitarity on every load (divides by N = |u01|^2 + |u02|^2: links with
+                        N = 0 keep only their row 0, the 2x2 block becomes e^{-i arg(u00)/2} 1) */
+#define GF_FP64_8 5  /* the same 8 reals in FP64 */
 
 /* creation flags */
 #define GF_FLAG_MIXED 1 /* keep an FP64-18 copy: gf_fix runs the FP32 storage down to the
-                           switch threshold, converts, then polishes in FP64 */
+                           switch threshold, converts, then polishes in FP64 (ignored for
+                           the FP64 storages) */
 #define GF_FLAG_AUTOGRAD 4 /* add the buffers of gf_ad_functional / gf_ad_backward (one
                               lattice, GF_FP64_18) */
 #define GF_FLAG_FASD 2  /* add the buffers of Fourier-accelerated steepest descent (one
@@ -85,8 +91,8 @@ typedef struct gf_handle gf_handle;
 /*
  * Bytes of device workspace a handle needs.
  *   n_lat: number of lattices (1 for gf_create); dims: n_lat * 4 ints as above;
- *   gauge: GF_LANDAU | GF_COULOMB; storage: GF_FP64_18 | GF_FP32_18 | GF_FP32_12;
- *   flags: 0 or GF_FLAG_MIXED.  *bytes receives the size.  Returns GF_EINVAL on bad
+ *   gauge: GF_LANDAU | GF_COULOMB; storage: one of the GF_FP* codes above;
+ *   flags: 0 or a combination of GF_FLAG_* (GF_FLAG_MIXED for the FP32 storages).  *bytes receives the size.  Returns GF_EINVAL on bad
  *   arguments.
  */
 GF_API int gf_workspace_bytes(int n_lat, const int *dims, int gauge, int storage, int flags,
@@ -129,13 +135,13 @@ GF_API int gf_num_units(const gf_handle *h);
  * sites, each complex element of a link at a stride of 4 V).
  *   links: canonical layout, 2*9*4*V float64; on_device = 1 if it is device memory,
  *   0 if host memory (pinned memory gives the fastest copies).
- *   Upload rounds to the handle's storage (FP32 and/or 12 reals: row 2 is dropped) and
- *   resets the sweep count (gf_get_sweeps_done), the masks (all units active) and the
- *   iteration counts.
- *   Download reconstructs row 2 in FP64 for 12-real storage.  In mixed mode gf_fix
- *   leaves the field in the FP64 copy and download reads that copy; an upload moves
- *   the handle back to its primary storage, so upload every lattice of a batch before
- *   the next gf_fix.  Device buffers must be 16-byte aligned.  Both calls synchronise
+ *   Upload rounds to the handle's storage (FP32 and/or 12 or 8 reals: the other
+ *   elements are dropped) and resets the sweep count (gf_get_sweeps_done), the masks
+ *   (all units active) and the iteration counts.  Download rebuilds the dropped
+ *   elements (rows 0, 1 of 8-real storage in the storage's precision, row 2 in FP64).
+ *   In mixed mode gf_fix leaves the field in the FP64 copy and download reads that copy;
+ *   an upload moves the handle back to its primary storage, so upload every lattice of
+ *   a batch before the next gf_fix.  Device buffers must be 16-byte aligned.  Both calls synchronise
  *   the stream when on_device = 0 (the host buffer is complete on return).
  */
 GF_API int gf_upload(gf_handle *h, int lat, const double *links, int on_device);
@@ -222,9 +228,10 @@ GF_API int gf_set_overrelax_form(gf_handle *h, int form);     /* [GF_OR_FIRST_OR
 GF_API int gf_set_reunit_interval(gf_handle *h, int n);       /* [20], 0 = never              */
 GF_API int gf_set_check_interval(gf_handle *h, int n);        /* [1], >= 1                    */
 GF_API int gf_set_mixed_switch(gf_handle *h, double eps_sw);  /* [1e-8], > 0                  */
-GF_API int gf_set_reproducible(gf_handle *h, int on);         /* [0]; 1 = FP64 kernels without
+GF_API int gf_set_reproducible(gf_handle *h, int on);         /* [0]; 1 = FP64-18 sweeps without
                                   fused multiply-add and with IEEE divisions, in the
-                                  oracle's operation order (bit-reproducible results) */
+                                  oracle's operation order (bit-reproducible results);
+                                  no effect on the other storages */
 GF_API int gf_set_block_size(gf_handle *h, int threads);      /* [128]; 64, 128 or 256        */
 
 /* Half-sweep kernel for FP32-12 storage: GF_SWEEP_REGISTER holds each site's 8 links in

@@ -31,6 +31,7 @@ UNITS = {
     "gf_inst_split.cu": [],
     "gf_inst_fasd.cu": [],
     "gf_inst_autograd.cu": [],
+    "gf_inst_compact.cu": [],
 }
 
 

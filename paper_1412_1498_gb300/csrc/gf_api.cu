@@ -48,10 +48,24 @@ void launch_measure_fp32(int storage, int nd, const MeasureArgs& a, int n_tiles,
                          cudaStream_t s);
 void launch_fill_int(int* p, int value, int n, cudaStream_t s);
 
+void launch_sweep_compact(int storage, int nd, const SweepArgs& a, int n_tiles, int threads,
+                          cudaStream_t s);
+void launch_measure_compact(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
+                            cudaStream_t s);
+
+bool is_fp64_storage(int storage) {
+  return storage == GF_FP64_18 || storage == GF_FP64_12 || storage == GF_FP64_8;
+}
+bool is_compact_storage(int storage) {
+  return storage == GF_FP64_12 || storage == GF_FP64_8 || storage == GF_FP32_8;
+}
+
 void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs& a, int n_tiles,
                   int threads, cudaStream_t s) {
   if (storage == kSplit18) {
     launch_sweep_split(nd, a, n_tiles, threads, s);
+  } else if (is_compact_storage(storage)) {
+    launch_sweep_compact(storage, nd, a, n_tiles, threads, s);
   } else if (storage == GF_FP64_18) {
     if (repro) launch_sweep_fp64_repro(nd, a, n_tiles, threads, s);
     else launch_sweep_fp64(nd, a, n_tiles, threads, s);
@@ -65,6 +79,7 @@ void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs&
 void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
                     cudaStream_t s) {
   if (storage == kSplit18) launch_measure_split(nd, a, n_tiles, threads, s);
+  else if (is_compact_storage(storage)) launch_measure_compact(storage, nd, a, n_tiles, threads, s);
   else if (storage == GF_FP64_18) launch_measure_fp64(nd, a, n_tiles, threads, s);
   else launch_measure_fp32(storage, nd, a, n_tiles, threads, s);
 }
@@ -90,7 +105,14 @@ constexpr int kGraphSweeps = 16;
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 int link_bytes(int storage) {
-  return storage == GF_FP64_18 ? 144 : storage == GF_FP32_18 ? 72 : 48;
+  switch (storage) {
+    case GF_FP64_18: return 144;
+    case GF_FP64_12: return 96;
+    case GF_FP32_18: return 72;
+    case GF_FP64_8: return 64;
+    case GF_FP32_8: return 32;
+    default: return 48;  // GF_FP32_12
+  }
 }
 
 struct Layout {
@@ -132,7 +154,7 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
     n_units += gauge == GF_LANDAU ? 1 : d[3];
   }
   L->links = take((size_t)sites * 4 * link_bytes(storage));
-  const bool mixed = (flags & GF_FLAG_MIXED) && storage != GF_FP64_18;
+  const bool mixed = (flags & GF_FLAG_MIXED) && !is_fp64_storage(storage);
   L->links64 = mixed ? take((size_t)sites * 4 * 144) : (size_t)-1;
   size_t canon = (size_t)vmax * 4 * 144;
   size_t site_bytes = 4 * 144;
@@ -185,8 +207,8 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
 int check_common(int n_lat, const int* dims, int gauge, int storage, int flags, std::string* why) {
   if (n_lat < 1 || !dims) { *why = "need at least one lattice"; return GF_EINVAL; }
   if (gauge != GF_LANDAU && gauge != GF_COULOMB) { *why = "gauge must be GF_LANDAU or GF_COULOMB"; return GF_EINVAL; }
-  if (storage != GF_FP64_18 && storage != GF_FP32_18 && storage != GF_FP32_12) {
-    *why = "storage must be GF_FP64_18, GF_FP32_18 or GF_FP32_12";
+  if (storage < GF_FP64_18 || storage > GF_FP64_8) {
+    *why = "storage must be one of GF_FP64_18, GF_FP32_18, GF_FP32_12, GF_FP64_12, GF_FP32_8, GF_FP64_8";
     return GF_EINVAL;
   }
   if (flags & ~(GF_FLAG_MIXED | GF_FLAG_FASD | GF_FLAG_AUTOGRAD)) { *why = "unknown flag"; return GF_EINVAL; }
@@ -196,7 +218,7 @@ int check_common(int n_lat, const int* dims, int gauge, int storage, int flags, 
   }
   if (flags & GF_FLAG_FASD) {
     if (n_lat != 1) { *why = "Fourier-accelerated steepest descent takes one lattice per handle"; return GF_EINVAL; }
-    if (storage == GF_FP32_18) { *why = "Fourier acceleration supports GF_FP32_12 and GF_FP64_18 storage"; return GF_EINVAL; }
+    if (storage != GF_FP32_12 && storage != GF_FP64_18) { *why = "Fourier acceleration supports GF_FP32_12 and GF_FP64_18 storage"; return GF_EINVAL; }
     const int nfft = gauge == GF_LANDAU ? 4 : 3;
     for (int k = 0; k < nfft; ++k) {
       const int L = dims[k];
@@ -211,14 +233,22 @@ int check_common(int n_lat, const int* dims, int gauge, int storage, int flags, 
       return GF_EINVAL;
     }
   }
-  for (int l = 0; l < n_lat; ++l)
-    if (!valid_dims(dims + 4 * l)) {
+  for (int l = 0; l < n_lat; ++l) {
+    const int* d = dims + 4 * l;
+    if (!valid_dims(d)) {
       char buf[160];
       snprintf(buf, sizeof buf, "lattice %d: every extent must be even and >= 2 (got %d %d %d %d)", l,
-               dims[4 * l], dims[4 * l + 1], dims[4 * l + 2], dims[4 * l + 3]);
+               d[0], d[1], d[2], d[3]);
       *why = buf;
       return GF_EINVAL;
     }
+    // the kernels divide slice indices by Lx and Ly with 32-bit reciprocal multiplies
+    const unsigned long long v3 = (unsigned long long)d[0] * d[1] * d[2];
+    if (v3 * (unsigned long long)(d[0] > d[1] ? d[0] : d[1]) >= (1ULL << 32)) {
+      *why = "Lx * Ly * Lz * max(Lx, Ly) must be below 2^32";
+      return GF_EINVAL;
+    }
+  }
   return GF_OK;
 }
 
@@ -612,7 +642,7 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   h->gauge = gauge;
   h->nd = gauge == GF_LANDAU ? 4 : 3;
   h->storage = storage;
-  h->flags = (storage == GF_FP64_18) ? (flags & ~GF_FLAG_MIXED) : flags;
+  h->flags = is_fp64_storage(storage) ? (flags & ~GF_FLAG_MIXED) : flags;
   h->dims.assign(dims, dims + 4 * n_lat);
   h->stream = (cudaStream_t)stream;
   plan(n_lat, dims, gauge, storage, h->flags, &h->L);
@@ -688,6 +718,8 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
     d.V = (long long)d.L[0] * d.L[1] * d.L[2] * d.L[3];
     d.Vh = (int)(d.V / 2);
     d.V3h = d.L[0] * d.L[1] * d.L[2] / 2;
+    d.mx = (unsigned int)(((1ULL << 32) + (unsigned long long)d.L[0] - 1) / (unsigned long long)d.L[0]);
+    d.my = (unsigned int)(((1ULL << 32) + (unsigned long long)d.L[1] - 1) / (unsigned long long)d.L[1]);
     d.unit0 = unit;
     d.n_units = gauge == GF_LANDAU ? 1 : d.L[3];
     unit += d.n_units;
@@ -840,7 +872,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
     if (h->cur != 0) return fail(h, GF_ESTATE, "upload the field before a Fourier-accelerated fix");
     if ((rc = run_fasd(h, eps, maxiter, &done)) != GF_OK) return rc;
     h->sweeps_done += done;
-    h->phase_sweeps[h->storage == GF_FP64_18 ? 1 : 0] = done;
+    h->phase_sweeps[is_fp64_storage(h->storage) ? 1 : 0] = done;
     if ((rc = copy_out(h, F, theta, nullptr, nullptr, iters)) != GF_OK) return rc;
     DevState s{};
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
@@ -883,7 +915,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
   } else {
     if ((rc = run_phase(h, eps, maxiter, &done)) != GF_OK) return rc;
     h->sweeps_done += done;
-    h->phase_sweeps[h->cur == 1 || h->storage == GF_FP64_18 ? 1 : 0] = done;
+    h->phase_sweeps[h->cur == 1 || is_fp64_storage(h->storage) ? 1 : 0] = done;
   }
   if ((rc = copy_out(h, F, theta, nullptr, nullptr, iters)) != GF_OK) return rc;
   DevState s{};

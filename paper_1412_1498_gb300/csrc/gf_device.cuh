@@ -11,6 +11,10 @@
 //   GF_FP32_12: 3 float4 planes, two complex elements per word: (U00,U01) (U02,U10)
 //               (U11,U12); row 2 = conj(row0 x row1) is rebuilt on every load.
 //   GF_FP32_18: 4 float4 planes (U00..U21) then one float2 plane (U22).
+//   GF_FP64_12: 6 double2 planes (U00..U12); row 2 rebuilt on every load.
+//   GF_FP32_8:  2 float4 planes (U01,U02) (U10, arg U00, arg U20).
+//   GF_FP64_8:  4 double2 planes U01, U02, U10, (arg U00, arg U20).
+//               Rows 0 and 1 are rebuilt from the 8 reals on every load (Store8 below).
 //
 // Consecutive threads take consecutive h of one parity, so every forward link load is
 // a contiguous run and every backward link U_mu(x - mu) a shifted contiguous run (mu >
@@ -40,6 +44,7 @@ struct LatDev {
   long long off_bytes;  // start of this lattice's link region in the link buffer
   int unit0;            // first convergence unit of this lattice
   int n_units;          // 1 (Landau) or Lt (Coulomb)
+  unsigned int mx, my;  // ceil(2^32 / Lx), ceil(2^32 / Ly): n / L = umulhi(n, m) for n L < 2^32
 };
 
 // One block of sites of one lattice, one time slice: (lat, t, first h3, unit)
@@ -100,6 +105,10 @@ template <>
 __device__ __forceinline__ double gf_sqrt<double>(double x) { return sqrt(x); }
 template <>
 __device__ __forceinline__ float gf_sqrt<float>(float x) { return sqrtf(x); }
+__device__ __forceinline__ void gf_sincos(double x, double* s, double* c) { sincos(x, s, c); }
+__device__ __forceinline__ void gf_sincos(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ double gf_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float gf_atan2(float y, float x) { return atan2f(y, x); }
 
 // ----------------------------------------------------------------------------------
 // Storage formats: load / store the stored complex elements of one link
@@ -181,6 +190,130 @@ struct Store<GF_FP32_18> {
           make_float4(e[2 * w].re, e[2 * w].im, e[2 * w + 1].re, e[2 * w + 1].im);
     float2* q = reinterpret_cast<float2*>(base + 256LL * V);
     q[(long long)mu * V + idx] = make_float2(e[8].re, e[8].im);
+  }
+};
+
+template <>
+struct Store<GF_FP64_12> {
+  using T = double;
+  static constexpr int NE = 6;
+  static constexpr int LINK_BYTES = 96;
+  __device__ static __forceinline__ void load(const char* base, long long V, int mu, int idx,
+                                              cx<T> (&e)[NE]) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+#pragma unroll
+    for (int w = 0; w < 6; ++w) {
+      double2 v = p[(long long)(w * 4 + mu) * V + idx];
+      e[w] = {v.x, v.y};
+    }
+  }
+  __device__ static __forceinline__ void store(char* base, long long V, int mu, int idx,
+                                               const cx<T> (&e)[NE]) {
+    double2* p = reinterpret_cast<double2*>(base);
+#pragma unroll
+    for (int w = 0; w < 6; ++w) p[(long long)(w * 4 + mu) * V + idx] = make_double2(e[w].re, e[w].im);
+  }
+};
+
+// 8-real parametrisation of an SU(3) link (the paper's third storage option, Section 2):
+// stored u01, u02, u10 and the phases of u00 and u20.  Unitarity gives the moduli,
+//   N = |u01|^2 + |u02|^2,  |u00| = sqrt(1 - N),  |u20| = sqrt(N - |u10|^2),
+// and, with conj(U) = cofactor matrix of U (U^-1 = U^+ and det U = 1), the two linear
+// equations  u01 u12 - u02 u11 = conj(u20)  and  conj(u00) u10 + conj(u01) u11 +
+// conj(u02) u12 = 0  (rows 0 and 1 orthogonal) give, by Cramer's rule (determinant -N),
+//   u11 = -(conj(u20) conj(u02) + conj(u00) u01 u10) / N,
+//   u12 =  (conj(u20) conj(u01) - conj(u00) u02 u10) / N.
+// N is formed from the stored u01, u02 (full relative precision near the identity).
+// At N = 0 (row 0 = (e^{i phi}, 0, 0)) the stored reals do not fix the 2x2 block;
+// it is taken as e^{-i phi / 2} times the identity (exact for diagonal links with that
+// block, e.g. the unit link).  In-register form: rows 0 and 1 (NE = 6, as 12-real).
+template <class T>
+struct Store8 {
+  static constexpr int NE = 6;
+  __device__ static __forceinline__ void rebuild(cx<T> u01, cx<T> u02, cx<T> u10, T ph0, T ph2,
+                                                 cx<T> (&e)[NE]) {
+    const T N = cnorm2(u01) + cnorm2(u02);
+    T s0, c0;
+    gf_sincos(ph0, &s0, &c0);
+    const T m0 = gf_sqrt(N < T(1) ? T(1) - N : T(0));
+    const cx<T> u00 = {m0 * c0, m0 * s0};
+    cx<T> u11, u12;
+    if (N > T(0)) {
+      T s2, c2;
+      gf_sincos(ph2, &s2, &c2);
+      const T d = N - cnorm2(u10);
+      const T m2 = gf_sqrt(d > T(0) ? d : T(0));
+      const cx<T> c20 = {m2 * c2, -(m2 * s2)};  // conj(u20)
+      const cx<T> c00u10 = cmul(cconj(u00), u10);
+      const T inv = T(1) / N;
+      u11 = cscale(cneg(cadd(cmul(c20, cconj(u02)), cmul(u01, c00u10))), inv);
+      u12 = cscale(csub(cmul(c20, cconj(u01)), cmul(u02, c00u10)), inv);
+    } else {
+      T sh, ch;
+      gf_sincos(T(-0.5) * ph0, &sh, &ch);
+      u11 = {ch, sh};
+      u12 = {T(0), T(0)};
+    }
+    e[0] = u00;
+    e[1] = u01;
+    e[2] = u02;
+    e[3] = u10;
+    e[4] = u11;
+    e[5] = u12;
+  }
+  // the 8 reals of rows 0, 1 (u20 = conj(u01 u12 - u02 u11), element 0 of row 2)
+  __device__ static __forceinline__ void reduce(const cx<T> (&e)[NE], T& ph0, T& ph2) {
+    const cx<T> u20 = cconj(csub(cmul(e[1], e[5]), cmul(e[2], e[4])));
+    ph0 = gf_atan2(e[0].im, e[0].re);
+    ph2 = gf_atan2(u20.im, u20.re);
+  }
+};
+
+template <>
+struct Store<GF_FP32_8> {
+  using T = float;
+  static constexpr int NE = 6;
+  static constexpr int LINK_BYTES = 32;
+  __device__ static __forceinline__ void load(const char* base, long long V, int mu, int idx,
+                                              cx<T> (&e)[NE]) {
+    const float4* p = reinterpret_cast<const float4*>(base);
+    const float4 a = p[(long long)mu * V + idx];
+    const float4 b = p[(long long)(4 + mu) * V + idx];
+    Store8<float>::rebuild({a.x, a.y}, {a.z, a.w}, {b.x, b.y}, b.z, b.w, e);
+  }
+  __device__ static __forceinline__ void store(char* base, long long V, int mu, int idx,
+                                               const cx<T> (&e)[NE]) {
+    float ph0, ph2;
+    Store8<float>::reduce(e, ph0, ph2);
+    float4* p = reinterpret_cast<float4*>(base);
+    p[(long long)mu * V + idx] = make_float4(e[1].re, e[1].im, e[2].re, e[2].im);
+    p[(long long)(4 + mu) * V + idx] = make_float4(e[3].re, e[3].im, ph0, ph2);
+  }
+};
+
+template <>
+struct Store<GF_FP64_8> {
+  using T = double;
+  static constexpr int NE = 6;
+  static constexpr int LINK_BYTES = 64;
+  __device__ static __forceinline__ void load(const char* base, long long V, int mu, int idx,
+                                              cx<T> (&e)[NE]) {
+    const double2* p = reinterpret_cast<const double2*>(base);
+    const double2 a = p[(long long)mu * V + idx];
+    const double2 b = p[(long long)(4 + mu) * V + idx];
+    const double2 c = p[(long long)(8 + mu) * V + idx];
+    const double2 f = p[(long long)(12 + mu) * V + idx];
+    Store8<double>::rebuild({a.x, a.y}, {b.x, b.y}, {c.x, c.y}, f.x, f.y, e);
+  }
+  __device__ static __forceinline__ void store(char* base, long long V, int mu, int idx,
+                                               const cx<T> (&e)[NE]) {
+    double ph0, ph2;
+    Store8<double>::reduce(e, ph0, ph2);
+    double2* p = reinterpret_cast<double2*>(base);
+    p[(long long)mu * V + idx] = make_double2(e[1].re, e[1].im);
+    p[(long long)(4 + mu) * V + idx] = make_double2(e[2].re, e[2].im);
+    p[(long long)(8 + mu) * V + idx] = make_double2(e[3].re, e[3].im);
+    p[(long long)(12 + mu) * V + idx] = make_double2(ph0, ph2);
   }
 };
 
@@ -279,18 +412,27 @@ struct Site {
   long long lexi;
 };
 
-__device__ __forceinline__ Site site_of(const LatDev& lat, int parity, int h) {
-  long long s2 = 2LL * h;
+// Site with parity-split index h3 inside time slice t.  The divisions by Lx and Ly are
+// multiplications by the ceilings m = ceil(2^32 / L): with n = q L + r and m L = 2^32 + e
+// (0 <= e < L), umulhi(n, m) = floor(n / L + n e / (L 2^32)) = q whenever n (L - 1) < 2^32,
+// which the handle checks at creation (Lx Ly Lz max(Lx, Ly) < 2^32).
+__device__ __forceinline__ Site site_of_slice(const LatDev& lat, int parity, int t, int h3) {
+  const unsigned s2 = 2u * (unsigned)h3;  // lexicographic index of (x0, y, z) in the slice
+  const unsigned q1 = __umulhi(s2, lat.mx);
+  const unsigned q2 = __umulhi(q1, lat.my);
   Site s;
-  int x0 = (int)(s2 % lat.L[0]);
-  long long r = s2 / lat.L[0];
-  s.y = (int)(r % lat.L[1]);
-  r /= lat.L[1];
-  s.z = (int)(r % lat.L[2]);
-  s.t = (int)(r / lat.L[2]);
+  const int x0 = (int)(s2 - q1 * (unsigned)lat.L[0]);
+  s.y = (int)(q1 - q2 * (unsigned)lat.L[1]);
+  s.z = (int)q2;
+  s.t = t;
   s.x = x0 + ((s.y + s.z + s.t + parity) & 1);
-  s.lexi = s2 + (s.x - x0);
+  s.lexi = (long long)t * (2LL * lat.V3h) + (long long)(s2 + (unsigned)(s.x - x0));
   return s;
+}
+
+__device__ __forceinline__ Site site_of(const LatDev& lat, int parity, int h) {
+  const int t = h / lat.V3h;
+  return site_of_slice(lat, parity, t, h - t * lat.V3h);
 }
 
 // lexicographic index of x - mu_hat (periodic)

@@ -192,6 +192,9 @@ static unsigned int blocks_for(long long n, int threads) { return (unsigned int)
   switch (storage) {                                   \
     case GF_FP64_18: CALL(GF_FP64_18); break;          \
     case GF_FP32_18: CALL(GF_FP32_18); break;          \
+    case GF_FP64_12: CALL(GF_FP64_12); break;          \
+    case GF_FP32_8: CALL(GF_FP32_8); break;            \
+    case GF_FP64_8: CALL(GF_FP64_8); break;            \
     default: CALL(GF_FP32_12); break;                  \
   }
 

@@ -17,6 +17,7 @@ void launch_to_split(int storage, const char* src, char* dst, const LatDev& ls, 
                      cudaStream_t s) {
   const unsigned int nb = (unsigned int)((4 * ls.V + 255) / 256);
   if (storage == GF_FP32_12) k_to_split<GF_FP32_12><<<nb, 256, 0, s>>>(src, dst, ls, ld);
+  else if (storage == GF_FP32_8) k_to_split<GF_FP32_8><<<nb, 256, 0, s>>>(src, dst, ls, ld);
   else k_to_split<GF_FP32_18><<<nb, 256, 0, s>>>(src, dst, ls, ld);
 }
 

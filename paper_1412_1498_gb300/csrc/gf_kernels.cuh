@@ -88,20 +88,24 @@ __device__ __forceinline__ void su2_left_mul(cx<T> (&M)[9], int i, int j, cx<T> 
 
 // G = product of the three subgroup maximisers for K (Cabibbo-Marinari order (0,1),
 // (0,2), (1,2)), K rotated after each one.
+// The first product R1 * 1 is R1 itself and K is not needed after the third step; both
+// shortcuts give the values of the plain sequence (x * 1 = x, x + 0 = x).
 template <class T, bool REPRO>
 __device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega, int form) {
-#pragma unroll
-  for (int e = 0; e < 9; ++e) G[e] = {T(0), T(0)};
-  G[0] = G[4] = G[8] = {T(1), T(0)};
   cx<T> a, b;
   su2_maximiser<T, REPRO>(K, 0, 1, omega, form, a, b);
   su2_left_mul(K, 0, 1, a, b);
-  su2_left_mul(G, 0, 1, a, b);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) G[e] = {T(0), T(0)};
+  G[0] = a;
+  G[1] = b;
+  G[3] = cneg(cconj(b));
+  G[4] = cconj(a);
+  G[8] = {T(1), T(0)};
   su2_maximiser<T, REPRO>(K, 0, 2, omega, form, a, b);
   su2_left_mul(K, 0, 2, a, b);
   su2_left_mul(G, 0, 2, a, b);
   su2_maximiser<T, REPRO>(K, 1, 2, omega, form, a, b);
-  su2_left_mul(K, 1, 2, a, b);
   su2_left_mul(G, 1, 2, a, b);
 }
 
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
-    const Site s = site_of(lat, p, h);
+    const Site s = site_of_slice(lat, p, tile.y, h3);
     char* base = a.links + lat.off_bytes;
     const long long V = lat.V;
     const int idx_f = p * lat.Vh + h;
@@ -386,7 +390,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
-    const Site s = site_of(lat, p, h);
+    const Site s = site_of_slice(lat, p, tile.y, h3);
     const char* base = a.links + lat.off_bytes;
     const int idx_f = p * lat.Vh + h;
     cx<T> A[9];

@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
-    const Site s = site_of(lat, p, h);
+    const Site s = site_of_slice(lat, p, tile.y, h3);
     char* base = a.links + lat.off_bytes;
     const long long V = lat.V;
     const int idx_f = p * lat.Vh + h;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(128) k_measure_split(MeasureArgs a) {
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
-    const Site s = site_of(lat, p, h);
+    const Site s = site_of_slice(lat, p, tile.y, h3);
     const char* base = a.links + lat.off_bytes;
     const int idx_f = p * lat.Vh + h;
     acc2 A[18];

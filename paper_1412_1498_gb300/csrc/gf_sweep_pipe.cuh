@@ -48,7 +48,7 @@ __device__ __forceinline__ PipeSite pipe_issue(const SweepArgs& a, int k, int bu
   if (ps.valid) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
-    const Site s = site_of(lat, p, h);
+    const Site s = site_of_slice(lat, p, tile.y, h3);
     ps.idx_f = p * lat.Vh + h;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) ps.idx_b[mu] = (1 - p) * lat.Vh + (int)(back_lexi(lat, s, mu) >> 1);

@@ -31,7 +31,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 # constants of include/gf.h
 GF_OK, GF_ENOTCONVERGED, GF_EINVAL, GF_ECUDA, GF_ENOMEM, GF_ESTATE = 0, 1, -1, -2, -3, -4
 GF_LANDAU, GF_COULOMB = 0, 1
-GF_FP64_18, GF_FP32_18, GF_FP32_12 = 0, 1, 2
+GF_FP64_18, GF_FP32_18, GF_FP32_12, GF_FP64_12, GF_FP32_8, GF_FP64_8 = 0, 1, 2, 3, 4, 5
 GF_FLAG_MIXED = 1
 GF_FLAG_FASD = 2
 GF_FLAG_AUTOGRAD = 4

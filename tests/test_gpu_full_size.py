@@ -38,8 +38,15 @@ def test_32x4_sweep_against_oracle(gf, field_32x4, storage):
     got = fx.download()
     ref = start.copy()
     oracle.sweep(ref, 1.7)
-    err = np.abs(got - ref).max()
-    assert err < (1e-13 if storage == gf.GF_FP64_18 else 5e-6), err
+    d = np.abs(got - ref)
+    err, rms = d.max(), float(np.sqrt(np.mean(d * d)))
+    if storage == gf.GF_FP64_18:
+        assert err < 1e-13, err
+    else:
+        # FP32 rounding, u = 2^-24: each element of a swept link carries O(10^3) rounding
+        # errors of size <= u (two site updates of ~2.3 kflop each), so its rms is a few u;
+        # the maximum over the 7.5e7 elements of a 32^4 field is a tail value (~170 u)
+        assert err < 1e-5 and rms < 1e-6, (err, rms)
     F, th, _, _ = oracle.measure(got)
     tol = 1e-12 if storage == gf.GF_FP64_18 else 1e-5
     assert abs(out["F"][0] - F) <= tol * abs(F) and abs(out["theta"][0] - th) <= tol * th
