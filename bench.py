@@ -231,8 +231,15 @@ def run_gpu(args):
     gf.gf_set_reunit_interval(fx.h, 20)
     fx.upload(U)
 
-    # ---- launch shape: the library's autotuner times every block size / kernel variant
-    best = gf.gf_autotune(fx.h)
+    # ---- launch shape: the library's autotuner times every block size / kernel variant,
+    # unless a shape is given (profiling runs: timings under a profiler mislead the tuner)
+    if args.launch:
+        t, v = args.launch.split(":")
+        best = (int(t), {"register": gf.GF_SWEEP_REGISTER, "pipelined": gf.GF_SWEEP_PIPELINED}[v])
+        gf.gf_set_block_size(fx.h, best[0])
+        gf.gf_set_sweep_variant(fx.h, best[1])
+    else:
+        best = gf.gf_autotune(fx.h)
     fx.upload(U)
 
     # ---- warm-up steps (untimed)
@@ -431,6 +438,8 @@ def main():
     ap.add_argument("--split-probe", type=int, default=100)
     ap.add_argument("--fasd-iters", type=int, default=50)
     ap.add_argument("--autograd", type=int, default=1)
+    ap.add_argument("--launch", default="", help="fixed launch shape THREADS:register|pipelined "
+                    "instead of the autotuner (for profiler runs)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "gf":
         args.warmup = 3

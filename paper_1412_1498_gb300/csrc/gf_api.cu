@@ -23,6 +23,7 @@ void launch_sweep_fp64(int nd, const SweepArgs& a, int n_tiles, int threads, cud
 void launch_sweep_fp64_repro(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_measure_fp32_pipe(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
 cudaError_t prepare_sweep_pipe();
 void launch_sweep_split(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_measure_split(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
@@ -76,8 +77,12 @@ void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs&
   }
 }
 
-void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,
-                    cudaStream_t s) {
+void launch_measure(int storage, int nd, int variant, const MeasureArgs& a, int n_tiles,
+                    int threads, cudaStream_t s) {
+  if (storage == GF_FP32_12 && variant != GF_SWEEP_REGISTER) {
+    launch_measure_fp32_pipe(nd, a, n_tiles, threads, s);
+    return;
+  }
   if (storage == kSplit18) launch_measure_split(nd, a, n_tiles, threads, s);
   else if (is_compact_storage(storage)) launch_measure_compact(storage, nd, a, n_tiles, threads, s);
   else if (storage == GF_FP64_18) launch_measure_fp64(nd, a, n_tiles, threads, s);
@@ -117,8 +122,8 @@ int link_bytes(int storage) {
 
 struct Layout {
   size_t links, links64, staging, lats, lats64, tiles, unit_tiles, unit_lat, active, iters, partF,
-      pthe, ptho, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT, unit_planes, ad_g,
-      ad_delta, ad_part, ad_ticket, total;
+      pthe, ptho, part_blk, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
+      unit_planes, ad_g, ad_delta, ad_part, ad_ticket, total;
   size_t staging_bytes;
   int max_tiles, n_units;
 };
@@ -144,15 +149,18 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
     return at;
   };
   long long sites = 0, vmax = 0;
-  int max_tiles = 0, n_units = 0;
+  int max_tiles = 0, n_units = 0, unit_tiles_max = 0;
   for (int l = 0; l < n_lat; ++l) {
     const int* d = dims + 4 * l;
     long long V = (long long)d[0] * d[1] * d[2] * d[3];
     sites += V;
     vmax = std::max(vmax, V);
-    max_tiles += tiles_for(d, kMinThreads);
+    const int nt = tiles_for(d, kMinThreads);
+    max_tiles += nt;
     n_units += gauge == GF_LANDAU ? 1 : d[3];
+    unit_tiles_max = std::max(unit_tiles_max, gauge == GF_LANDAU ? nt : nt / d[3]);
   }
+  const int fin_blocks = (unit_tiles_max + kFinishThreads - 1) / kFinishThreads;
   L->links = take((size_t)sites * 4 * link_bytes(storage));
   const bool mixed = (flags & GF_FLAG_MIXED) && !is_fp64_storage(storage);
   L->links64 = mixed ? take((size_t)sites * 4 * 144) : (size_t)-1;
@@ -170,6 +178,7 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->partF = take(sizeof(double) * max_tiles);
   L->pthe = take(sizeof(double) * max_tiles);
   L->ptho = take(sizeof(double) * max_tiles);
+  L->part_blk = take(sizeof(double) * 3 * (size_t)n_units * fin_blocks);
   L->usF = take(sizeof(double) * n_units);
   L->usT = take(sizeof(double) * n_units);
   L->uF = take(sizeof(double) * n_units);
@@ -267,7 +276,8 @@ struct gf_handle {
   LatDev *d_lats = nullptr, *d_lats64 = nullptr;
   int4* d_tiles = nullptr;
   int *d_unit_tiles = nullptr, *d_unit_lat = nullptr, *d_active = nullptr, *d_iters = nullptr;
-  double *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr;
+  double *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr, *d_part_blk = nullptr;
+  int fin_blocks = 1;  // finishing blocks per unit for the current tile table
   double *d_usF = nullptr, *d_usT = nullptr, *d_uF = nullptr, *d_uT = nullptr, *d_lF = nullptr,
          *d_lT = nullptr;
   DevState* d_state = nullptr;
@@ -357,6 +367,9 @@ int build_tiles(gf_handle* h) {
   unit_tiles.push_back((int)tiles.size());
   if ((int)tiles.size() > h->L.max_tiles) return fail(h, GF_EINVAL, "tile table overflow");
   h->n_tiles = (int)tiles.size();
+  int most = 1;
+  for (size_t u = 0; u + 1 < unit_tiles.size(); ++u) most = std::max(most, unit_tiles[u + 1] - unit_tiles[u]);
+  h->fin_blocks = (most + kFinishThreads - 1) / kFinishThreads;
   GF_CK(h, cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
   GF_CK(h, cudaMemcpyAsync(h->d_unit_tiles, unit_tiles.data(), sizeof(int) * unit_tiles.size(),
                            cudaMemcpyHostToDevice, h->stream));
@@ -410,6 +423,8 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   a.part_F = h->d_partF;
   a.part_th_even = h->d_pthe;
   a.part_th_odd = h->d_ptho;
+  a.part_blk = h->d_part_blk;
+  a.blocks_per_unit = h->fin_blocks;
   a.unit_sumF = h->d_usF;
   a.unit_sumTh = h->d_usT;
   a.unit_F = h->d_uF;
@@ -427,9 +442,9 @@ FinishArgs finish_args(gf_handle* h, int mode) {
 // F and theta of every unit and lattice, all units (mode MEASURE or RESET), async.
 int enqueue_measure_all(gf_handle* h, int mode) {
   const int st = cur_storage(h);
-  launch_measure(st, h->nd, measure_args(h, 0, false, 0), h->n_tiles, h->threads, h->stream);
+  launch_measure(st, h->nd, h->variant, measure_args(h, 0, false, 0), h->n_tiles, h->threads, h->stream);
   GF_CK_LAUNCH(h);
-  launch_measure(st, h->nd, measure_args(h, 1, false, 1), h->n_tiles, h->threads, h->stream);
+  launch_measure(st, h->nd, h->variant, measure_args(h, 1, false, 1), h->n_tiles, h->threads, h->stream);
   GF_CK_LAUNCH(h);
   launch_finish(finish_args(h, mode), h->stream);
   GF_CK_LAUNCH(h);
@@ -447,7 +462,7 @@ int enqueue_loop_sweep(gf_handle* h, cudaStream_t s, int* pass) {
   launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 1, true, (*pass)++ & 1), h->n_tiles,
                h->threads, s);
   GF_CK_LAUNCH(h);
-  launch_measure(st, h->nd, measure_args(h, 0, true, (*pass)++ & 1), h->n_tiles, h->threads, s);
+  launch_measure(st, h->nd, h->variant, measure_args(h, 0, true, (*pass)++ & 1), h->n_tiles, h->threads, s);
   GF_CK_LAUNCH(h);
   launch_finish(finish_args(h, FINISH_LOOP), s);
   GF_CK_LAUNCH(h);
@@ -686,6 +701,7 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   h->d_partF = (double*)(w + L.partF);
   h->d_pthe = (double*)(w + L.pthe);
   h->d_ptho = (double*)(w + L.ptho);
+  h->d_part_blk = (double*)(w + L.part_blk);
   h->d_usF = (double*)(w + L.usF);
   h->d_usT = (double*)(w + L.usT);
   h->d_uF = (double*)(w + L.uF);

@@ -3,74 +3,81 @@
 
 namespace gf {
 
-__global__ void __launch_bounds__(512) k_finish(FinishArgs a) {
-  __shared__ double red[96];
+// Two stages.  Block (u, j) adds tiles [j * kFinishThreads, (j + 1) * kFinishThreads) of
+// unit u with a fixed binary tree in shared memory (FP64 issues at ~1/64 of the FP32
+// rate here, so the tree does n - 1 additions instead of a shuffle tree's 5 n) and
+// stores the three sums.  The last block to take a ticket adds each unit's block sums
+// in order and finishes the unit (values, mask, iteration count), then the lattice
+// totals and the loop state.  The order of every addition is fixed: deterministic.
+__global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
+  __shared__ double red[3][kFinishThreads];
   __shared__ int s_last;
-  const int u = blockIdx.x;
-  bool loop = a.mode == FINISH_LOOP;
+  __shared__ int s_cnt[kFinishThreads / 32];
+  const int tid = (int)threadIdx.x;
+  const int S = a.blocks_per_unit;
+  const int u = (int)blockIdx.x / S, j = (int)blockIdx.x - u * S;
+  const bool loop = a.mode == FINISH_LOOP;
   bool check = true;
   if (loop) {
     if (!state_running(a.st)) return;  // uniform over the grid: nobody takes a ticket
     check = state_check_sweep(a.st);
   }
-  const bool was_active = a.active[u] != 0;
-  const bool reduce = loop ? (was_active && check) : true;
+  const bool reduce = loop ? (a.active[u] != 0 && check) : true;
   if (reduce) {
-    const int tb = a.unit_tiles[u], te = a.unit_tiles[u + 1];
-    // 8 independent accumulators per value so that the loads of a pass are all in
-    // flight together; combined in a fixed order (deterministic)
-    constexpr int U = 8;
-    double acc[3][U];
+    const int i = a.unit_tiles[u] + j * kFinishThreads + tid;
+    const bool in = i < a.unit_tiles[u + 1];
+    red[0][tid] = in ? a.part_F[i] : 0.0;
+    red[1][tid] = in ? a.part_th_even[i] : 0.0;
+    red[2][tid] = in ? a.part_th_odd[i] : 0.0;
+    __syncthreads();
 #pragma unroll
-    for (int k = 0; k < 3; ++k)
-#pragma unroll
-      for (int j = 0; j < U; ++j) acc[k][j] = 0.0;
-    const int stride = (int)blockDim.x;
-    for (int i0 = tb + (int)threadIdx.x; i0 < te; i0 += U * stride) {
-#pragma unroll
-      for (int j = 0; j < U; ++j) {
-        const int i = i0 + j * stride;
-        if (i < te) {
-          acc[0][j] += a.part_F[i];
-          acc[1][j] += a.part_th_even[i];
-          acc[2][j] += a.part_th_odd[i];
-        }
+    for (int w = kFinishThreads / 2; w > 0; w >>= 1) {
+      if (tid < w) {
+        red[0][tid] += red[0][tid + w];
+        red[1][tid] += red[1][tid + w];
+        red[2][tid] += red[2][tid + w];
       }
+      __syncthreads();
     }
-    double v[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-      v[k] = ((acc[k][0] + acc[k][1]) + (acc[k][2] + acc[k][3])) + ((acc[k][4] + acc[k][5]) + (acc[k][6] + acc[k][7]));
-    block_sum<3>(v, red);
-    if (threadIdx.x == 0) {
-      const LatDev lat = a.lats[a.unit_lat[u]];
-      const double vol = a.nd == 4 ? (double)lat.V : 2.0 * lat.V3h;  // Landau: V, Coulomb: slice
-      const double sF = v[0], sTh = v[1] + v[2];
-      a.unit_sumF[u] = sF;
-      a.unit_sumTh[u] = sTh;
-      a.unit_F[u] = sF / ((double)a.nd * 3.0 * vol);
-      a.unit_theta[u] = sTh / (3.0 * vol);
-    }
+    if (tid < 3) a.part_blk[3 * blockIdx.x + tid] = red[tid][0];
   }
-  if (threadIdx.x == 0) {
-    if (loop) {
-      if (was_active) {
-        a.iters[u] += 1;
-        if (check) a.active[u] = a.unit_theta[u] >= a.st->eps;
-      }
-    } else if (a.mode == FINISH_RESET) {
-      a.active[u] = a.unit_theta[u] >= a.st->eps;
-    }
+  __syncthreads();
+  if (tid == 0) {
     __threadfence();
     const unsigned int t = atomicAdd(&a.st->ticket, 1u);
-    s_last = (t == (unsigned int)(a.n_units - 1));
+    s_last = (t == gridDim.x - 1);
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last block: lattice totals in a fixed order, active count, loop state
+  // last block: every unit from its block sums, in order
+  for (int v = tid; v < a.n_units; v += blockDim.x) {
+    const bool was_active = __ldcg(a.active + v) != 0;
+    if (loop ? (was_active && check) : true) {
+      const int nb = (a.unit_tiles[v + 1] - a.unit_tiles[v] + kFinishThreads - 1) / kFinishThreads;
+      double sF = 0.0, sE = 0.0, sO = 0.0;
+      for (int b = 0; b < nb; ++b) {
+        const double* p = a.part_blk + 3 * (v * S + b);
+        sF += __ldcg(p);
+        sE += __ldcg(p + 1);
+        sO += __ldcg(p + 2);
+      }
+      const LatDev lat = a.lats[a.unit_lat[v]];
+      const double vol = a.nd == 4 ? (double)lat.V : 2.0 * lat.V3h;  // Landau: V, Coulomb: slice
+      const double sTh = sE + sO;
+      a.unit_sumF[v] = sF;
+      a.unit_sumTh[v] = sTh;
+      a.unit_F[v] = sF / ((double)a.nd * 3.0 * vol);
+      a.unit_theta[v] = sTh / (3.0 * vol);
+      // the loop reduces active units on check sweeps only; RESET re-derives every mask
+      if (loop || a.mode == FINISH_RESET) a.active[v] = sTh / (3.0 * vol) >= a.st->eps;
+    }
+    if (loop && was_active) a.iters[v] += 1;
+  }
+  __syncthreads();
+  // lattice totals in a fixed order, active count, loop state
   if (!loop || check) {
-    for (int l = threadIdx.x; l < a.n_lat; l += blockDim.x) {
+    for (int l = tid; l < a.n_lat; l += blockDim.x) {
       const LatDev lat = a.lats[l];
       double sF = 0.0, sTh = 0.0;
       for (int k = 0; k < lat.n_units; ++k) {
@@ -81,17 +88,23 @@ __global__ void __launch_bounds__(512) k_finish(FinishArgs a) {
       a.lat_theta[l] = sTh / (3.0 * (double)lat.V);
     }
   }
-  double c[1] = {0.0};
-  for (int k = threadIdx.x; k < a.n_units; k += blockDim.x) c[0] += (double)__ldcg(a.active + k);
-  block_sum<1>(c, red);
-  if (threadIdx.x == 0) {
-    if (a.mode != FINISH_MEASURE) a.st->n_active = (int)c[0];
+  int c = 0;
+  for (int k = tid; k < a.n_units; k += blockDim.x) c += __ldcg(a.active + k);
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((tid & 31) == 0) s_cnt[tid >> 5] = c;
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    for (int w = 0; w < kFinishThreads / 32; ++w) n += s_cnt[w];
+    if (a.mode != FINISH_MEASURE) a.st->n_active = n;
     if (loop) a.st->sweep += 1;
     a.st->ticket = 0u;
   }
 }
 
-void launch_finish(const FinishArgs& a, cudaStream_t s) { k_finish<<<a.n_units, 512, 0, s>>>(a); }
+void launch_finish(const FinishArgs& a, cudaStream_t s) {
+  k_finish<<<a.n_units * a.blocks_per_unit, kFinishThreads, 0, s>>>(a);
+}
 
 // ---------------------------------------------------------------------------------
 // element kernels

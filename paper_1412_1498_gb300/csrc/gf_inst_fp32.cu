@@ -7,6 +7,7 @@ namespace gf {
 namespace {
 constexpr int kMaxDev = 64;
 int g_pipe_grid[kMaxDev][2][3];  // [device][nd == 4][threads 64/128/256] persistent grid size
+int g_meas_grid[kMaxDev][2][3];  // the same for the pipelined F / theta pass
 }  // namespace
 
 static int threads_slot(int threads) { return threads == 64 ? 0 : threads == 128 ? 1 : 2; }
@@ -30,8 +31,30 @@ cudaError_t prepare_sweep_pipe() {
       if (e != cudaSuccess) return e;
       g_pipe_grid[dev][n][threads_slot(t)] = per_sm * sms;
     }
+    auto mk = n ? k_measure_pipe<4> : k_measure_pipe<3>;
+    const int words = 6 * (n ? 4 : 3);
+    e = cudaFuncSetAttribute(mk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * words * 256 * sizeof(float4)));
+    if (e != cudaSuccess) return e;
+    for (int t : {64, 128, 256}) {
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mk, t, 2 * words * t * sizeof(float4));
+      if (e != cudaSuccess) return e;
+      g_meas_grid[dev][n][threads_slot(t)] = per_sm * sms;
+    }
   }
   return cudaSuccess;
+}
+
+void launch_measure_fp32_pipe(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int grid = g_meas_grid[dev < kMaxDev ? dev : 0][nd == 4][threads_slot(threads)];
+  if (grid <= 0) grid = 1;
+  if (grid > n_tiles) grid = n_tiles;
+  const size_t smem = 2 * 6 * nd * threads * sizeof(float4);
+  if (nd == 4) k_measure_pipe<4><<<grid, threads, smem, s>>>(a);
+  else k_measure_pipe<3><<<grid, threads, smem, s>>>(a);
 }
 
 void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s) {

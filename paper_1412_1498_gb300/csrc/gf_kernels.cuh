@@ -198,9 +198,13 @@ struct MeasureArgs {
   int reverse;
 };
 
+constexpr int kFinishThreads = 256;  // tiles summed by one block of the finishing kernel
+
 struct FinishArgs {
   const LatDev* lats;
   const int* unit_tiles;   // n_units + 1 tile boundaries
+  double* part_blk;        // 3 sums per finishing block
+  int blocks_per_unit;     // finishing blocks per unit: ceil(max tiles of a unit / kFinishThreads)
   const int* unit_lat;     // lattice of each unit
   int* active;
   int* iters;
@@ -437,7 +441,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
 // lattice totals and the loop state.  One block per unit; the last block to finish
 // does the lattice totals (deterministic: fixed summation order everywhere).
 // ----------------------------------------------------------------------------------
-__global__ void __launch_bounds__(512) k_finish(FinishArgs a);
+__global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a);
 
 // ----------------------------------------------------------------------------------
 // Element kernels over all links: layout conversion, reunitarisation, FP32 -> FP64.
@@ -460,7 +464,8 @@ __global__ void k_to_fp64(const char* src, char* dst, LatDev lat_src, LatDev lat
 // ----------------------------------------------------------------------------------
 void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs& a, int n_tiles,
                   int threads, cudaStream_t s);
-void launch_measure(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
+void launch_measure(int storage, int nd, int variant, const MeasureArgs& a, int n_tiles, int threads,
+                    cudaStream_t s);
 void launch_finish(const FinishArgs& a, cudaStream_t s);
 void launch_pack(int storage, char* links, const LatDev& lat, const double* src, long long s0,
                  long long nsites, cudaStream_t s);

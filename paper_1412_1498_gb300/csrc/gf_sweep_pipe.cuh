@@ -155,4 +155,100 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
   }
 }
 
+// ----------------------------------------------------------------------------------
+// FP32-12 F / theta pass (Eqs. (1)-(3)) over the sites of one parity with the same
+// staging: each thread copies the 2 nd links of its site (6 nd words) one tile ahead
+// and reads back only what it copied.  The per-site arithmetic and the per-tile
+// reduction are k_measure's, so the tile partials are the same.
+// ----------------------------------------------------------------------------------
+struct MeasSite {
+  int ti;
+  bool active;
+  bool valid;
+};
+
+template <int ND>
+__device__ __forceinline__ MeasSite meas_issue(const MeasureArgs& a, int k, int buf, float4* sm) {
+  MeasSite ms;
+  ms.ti = a.reverse ? a.n_tiles - 1 - k : k;
+  const int4 tile = a.tiles[ms.ti];
+  ms.active = a.active == nullptr || a.active[tile.w] != 0;
+  const LatDev lat = a.lats[tile.x];
+  const int h3 = tile.z + (int)threadIdx.x;
+  ms.valid = ms.active && h3 < lat.V3h;
+  if (ms.valid) {
+    const int p = a.parity;
+    const Site s = site_of_slice(lat, p, tile.y, h3);
+    const int idx_f = p * lat.Vh + tile.y * lat.V3h + h3;
+    const float4* g = reinterpret_cast<const float4*>(a.links + lat.off_bytes);
+    const int B = blockDim.x;
+    float4* slot = sm + (buf * 6 * ND) * B + threadIdx.x;
+#pragma unroll
+    for (int mu = 0; mu < ND; ++mu) {
+      const int idx_b = (1 - p) * lat.Vh + (int)(back_lexi(lat, s, mu) >> 1);
+#pragma unroll
+      for (int w = 0; w < 3; ++w) {
+        cp_async16(slot + (3 * mu + w) * B, g + (long long)(w * 4 + mu) * lat.V + idx_f);
+        cp_async16(slot + (3 * ND + 3 * mu + w) * B, g + (long long)(w * 4 + mu) * lat.V + idx_b);
+      }
+    }
+  }
+  return ms;
+}
+
+template <int ND>
+__global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
+  extern __shared__ float4 sm[];
+  __shared__ double red[64];
+  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st))) return;
+  int k = blockIdx.x;
+  if (k >= a.n_tiles) return;
+  const int B = blockDim.x;
+  int buf = 0;
+  MeasSite cur = meas_issue<ND>(a, k, 0, sm);
+  cp_async_commit();
+  for (;;) {
+    const int kn = k + (int)gridDim.x;
+    MeasSite nxt;
+    if (kn < a.n_tiles) nxt = meas_issue<ND>(a, kn, buf ^ 1, sm);
+    cp_async_commit();
+    cp_async_wait_all_but_newest();  // this thread's copies of tile k have landed
+    if (cur.active) {                // uniform over the block
+      float fsum = 0.f, q = 0.f;
+      if (cur.valid) {
+        const float4* slot = sm + (buf * 6 * ND) * B + threadIdx.x;
+        cx<float> f[ND][6], b[ND][6];
+#pragma unroll
+        for (int nu = 0; nu < ND; ++nu) {
+          pipe_read(slot, B, 3 * nu, f[nu]);
+          pipe_read(slot, B, 3 * ND + 3 * nu, b[nu]);
+        }
+        cx<float> A[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) A[e] = {0.f, 0.f};
+        float fs = 0.f;
+#pragma unroll
+        for (int nu = 0; nu < ND; ++nu) {
+          fs = fs + (re_trace(f[nu]) + re_trace(b[nu]));
+          add_to_A(A, f[nu], b[nu]);
+        }
+        fsum = fs;
+        q = theta_site(A);
+      }
+      const float v[2] = {fsum, q};
+      double o[2];
+      block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
+      if (threadIdx.x == 0) {
+        if (a.part_F) a.part_F[cur.ti] = o[0];
+        a.part_theta[cur.ti] = o[1];
+      }
+      __syncthreads();  // red[] is reused by the next tile
+    }
+    if (kn >= a.n_tiles) break;
+    k = kn;
+    buf ^= 1;
+    cur = nxt;
+  }
+}
+
 }  // namespace gf

@@ -272,8 +272,9 @@ def test_block_sizes_agree(gf, threads):
 @pytest.mark.parametrize("gauge", [0, 1])
 @pytest.mark.parametrize("threads", [64, 128, 256])
 def test_pipelined_sweep_equals_register_sweep(gf, gauge, threads):
-    # the shared-memory pipelined FP32-12 kernel does the register kernel's arithmetic
-    # in the same order: same bits, with reunitarisation, checks and Coulomb masks
+    # the shared-memory pipelined FP32-12 kernels (sweep and F/theta pass) do the register
+    # kernels' arithmetic in the same order: same bits, with reunitarisation, checks and
+    # Coulomb masks
     dims = DIMS if gauge == 0 else DIMS_C
     U = fields.random_gauge_config(dims, 0.5, 72)
     outs = []
@@ -282,13 +283,15 @@ def test_pipelined_sweep_equals_register_sweep(gf, gauge, threads):
         gf.gf_set_sweep_variant(fx.h, variant)
         gf.gf_set_block_size(fx.h, threads)
         fx.upload(U)
+        m0 = [np.asarray(x).copy() for x in fx.functional_theta()]
         o1 = fx.fix(1e-300, 30)
         o2 = fx.fix(1e-6, 300)
-        outs.append((fx.download(), o1["F"][0], o1["theta"][0], o2["iters"].copy(), o2["theta"][0]))
+        outs.append((fx.download(), o1["F"][0], o1["theta"][0], o2["iters"].copy(), o2["theta"][0], m0))
         fx.close()
     a, b = outs
     assert np.array_equal(a[0], b[0])
     assert a[1:3] == b[1:3] and np.array_equal(a[3], b[3]) and a[4] == b[4]
+    assert all(np.array_equal(x, y) for x, y in zip(a[5], b[5]))
 
 
 # ---------------------------------------------------------------- double-float polish

@@ -53,7 +53,11 @@ def test_roundtrip(gf, storage):
     got = fx.download()
     if storage == gf.GF_FP64_12:
         assert np.array_equal(got[..., :2, :], U[..., :2, :])
-        assert np.abs(got[..., 2, :] - U[..., 2, :]).max() < 8 * U64
+        # row 2 = conj(row0 x row1) to a few roundings; U's own row 2 differs from that
+        # by U's unitarity defect
+        r2 = np.conj(np.cross(U[..., 0, :], U[..., 1, :]))
+        assert np.abs(got[..., 2, :] - r2).max() < 8 * U64
+        assert np.abs(got[..., 2, :] - U[..., 2, :]).max() < 8 * U64 + np.abs(U[..., 2, :] - r2).max()
     else:
         # the stored elements come back as stored (FP32: rounded once)
         dt = np.complex64 if storage == gf.GF_FP32_8 else np.complex128
@@ -165,21 +169,30 @@ def test_fp32_8_sweeps_against_fp64_oracle(gf, gauge):
 
 
 def test_fp32_8_mixed_reaches_1e15(gf):
-    # the 8^4 workload through the FP32 8-real phase and the FP64 polish
+    # the 8^4 workload through the FP32 8-real phase and the FP64 polish.  The FP32 phase
+    # moves the field off its gauge orbit by the rebuild error of every store, so the
+    # polish is checked against the oracle started from the field at the switch: the
+    # same FP32 phase run alone (same kernels, same sweeps), converted to FP64 and
+    # reunitarised as the mixed run does
     dims = (8, 8, 8, 8)
     U = fields.random_gauge_config(dims, 0.4, 1, 2)
-    ref = U.copy()
-    r = oracle.fix(ref, 1e-15, 3000, 1.7)
+    fa = gf.GaugeFixer(dims, gf.GF_LANDAU, gf.GF_FP32_8)
+    fa.upload(U)
+    oa = fa.fix(1e-8, 3000)
+    Vs = fa.download()
+    fa.close()
     fx = gf.GaugeFixer(dims, gf.GF_LANDAU, gf.GF_FP32_8, mixed=True)
     fx.upload(U)
     out = fx.fix(1e-15, 3000)
     assert out["rc"] == gf.GF_OK
     n32, n64 = out["phase_sweeps"]
-    assert n32 > 0 and n64 > 0
+    assert n32 == oa["iters"][0] and n64 > 0
     got = fx.download()
     F, th, _, _ = oracle.measure(got)
     assert th < 1e-15 * (1 + 1e-6)
-    assert abs(F - r["F"]) < 1e-6                   # same maximum (FP32 phase: ~1e-7 drift)
+    ref = oracle.reunit(np.ascontiguousarray(Vs))
+    r = oracle.fix(ref, 1e-15, 3000, 1.7)
+    assert abs(F - r["F"]) <= 1e-12 * abs(r["F"])
     fx.close()
 
 
