@@ -37,9 +37,13 @@ EPS_FIELD, SEED = 0.5, 3
 OMEGA = 1.7
 LINK_B = 48                    # FP32, 12 reals
 V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
-STEP_BYTES = 20 * V * LINK_B   # sweep 16 V b + theta pass 4 V b
+# One step = one sweep and its stop check.  Algorithmic bytes: the sweep reads and writes
+# every link twice (16 V b); the check adds nothing where it is fused (F and the odd-site
+# theta in the odd half-sweep) and 4 V b on the sweeps whose odd part alone cannot decide.
+STEP_BYTES = 16 * V * LINK_B
+CHECK_BYTES = 4 * V * LINK_B
 HALF_SWEEP_BYTES = 8 * V * LINK_B
-WORKLOAD = "landau-32^4-fp32-12: OR sweep (even+odd, omega 1.7, reunit every 20) + F/theta"
+WORKLOAD = "landau-32^4-fp32-12: OR sweep (even+odd, omega 1.7, reunit every 20) + F/theta stop check"
 
 
 def profiled_traffic(profile: str, sources) -> int | None:
@@ -181,7 +185,7 @@ def run_reference(args):
     oracle_steps(U, max_steps=args.steps, first=args.warmup)
     el = time.perf_counter() - t0
     vol = dims[0] * dims[1] * dims[2] * dims[3]
-    value = 20 * vol * LINK_B * args.steps / el / 1e9
+    value = 16 * vol * LINK_B * args.steps / el / 1e9
     sample = (f"{args.steps} steps on a {'x'.join(map(str, dims))} lattice of the 32^4 workload's "
               "field recipe (FP64 oracle, 18 reals per link, OpenMP over one parity)")
     print(json.dumps({
@@ -267,10 +271,12 @@ def run_gpu(args):
         k1.synchronize()
         half_ms = k0.elapsed_time(k1) / n_half
     assert int(iters[0]) == args.steps, (iters, args.steps)
-    ms_total, value = reduce_over_ranks(ms_total, args.steps, world, STEP_BYTES, dist, dev)
+    # the last sweep of the budget always takes the exact (even-site) check
+    bytes_per_step = STEP_BYTES + CHECK_BYTES / args.steps
+    ms_total, value = reduce_over_ranks(ms_total, args.steps, world, bytes_per_step, dist, dev)
     ms_step = ms_total / args.steps
     graph_sweeps = 16
-    launches = 3 + ((args.steps + graph_sweeps - 1) // graph_sweeps) * graph_sweeps * 4
+    launches = 3 + ((args.steps + graph_sweeps - 1) // graph_sweeps) * graph_sweeps * 5
 
     # ---- end to end through the C ABI with pinned host buffers: upload, one step, download
     Uh = torch.from_numpy(U).pin_memory()
@@ -284,7 +290,7 @@ def run_gpu(args):
         fx.download(out=out)
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0) / e2e_steps
-    e2e_value = world * STEP_BYTES / e2e_s / 1e9
+    e2e_value = world * (STEP_BYTES + CHECK_BYTES) / e2e_s / 1e9  # a 1-sweep fix checks exactly
     canon_bytes = 4 * V * 144
 
     # ---- time to theta < 1e-15: mixed FP32-12 -> FP64-18 vs pure FP64-18
@@ -413,6 +419,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": canon_bytes,
                     "d2h_bytes_per_step": canon_bytes},
             "gpu_launches": launches,
+            "sweeps_per_s": world * args.steps / (ms_total * 1e-3),
             "clocks": clocks.summary(),
             "time_to_theta_1e-15": ttt,
             "split_polish_probe": split_probe,

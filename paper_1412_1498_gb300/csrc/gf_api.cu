@@ -122,7 +122,7 @@ int link_bytes(int storage) {
 
 struct Layout {
   size_t links, links64, staging, lats, lats64, tiles, unit_tiles, unit_lat, active, iters, partF,
-      pthe, ptho, part_blk, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
+      pthe, ptho, part_blk, pending, usTo, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
       unit_planes, ad_g, ad_delta, ad_part, ad_ticket, total;
   size_t staging_bytes;
   int max_tiles, n_units;
@@ -179,6 +179,8 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->pthe = take(sizeof(double) * max_tiles);
   L->ptho = take(sizeof(double) * max_tiles);
   L->part_blk = take(sizeof(double) * 3 * (size_t)n_units * fin_blocks);
+  L->pending = take(sizeof(int) * n_units);
+  L->usTo = take(sizeof(double) * n_units);
   L->usF = take(sizeof(double) * n_units);
   L->usT = take(sizeof(double) * n_units);
   L->uF = take(sizeof(double) * n_units);
@@ -276,7 +278,9 @@ struct gf_handle {
   LatDev *d_lats = nullptr, *d_lats64 = nullptr;
   int4* d_tiles = nullptr;
   int *d_unit_tiles = nullptr, *d_unit_lat = nullptr, *d_active = nullptr, *d_iters = nullptr;
-  double *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr, *d_part_blk = nullptr;
+  double *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr, *d_part_blk = nullptr,
+         *d_usTo = nullptr;
+  int* d_pending = nullptr;
   int fin_blocks = 1;  // finishing blocks per unit for the current tile table
   double *d_usF = nullptr, *d_usT = nullptr, *d_uF = nullptr, *d_uT = nullptr, *d_lF = nullptr,
          *d_lT = nullptr;
@@ -390,6 +394,7 @@ SweepArgs sweep_args(gf_handle* h, int parity, bool loop, int reverse) {
   a.active = loop ? h->d_active : nullptr;
   a.st = loop ? h->d_state : nullptr;
   a.part_theta = h->d_ptho;
+  a.part_F = loop && parity == 1 ? h->d_partF : nullptr;
   a.parity = parity;
   a.form = h->form;
   a.reunit = 0;
@@ -405,9 +410,11 @@ MeasureArgs measure_args(gf_handle* h, int parity, bool loop, int reverse) {
   a.links = cur_links(h);
   a.lats = cur_lats(h);
   a.tiles = h->d_tiles;
-  a.active = loop ? h->d_active : nullptr;
+  // in the loop the even-site pass serves the units pending after the odd half-sweep,
+  // which already measured F
+  a.active = loop ? h->d_pending : nullptr;
   a.st = loop ? h->d_state : nullptr;
-  a.part_F = parity == 0 ? h->d_partF : nullptr;
+  a.part_F = parity == 0 && !loop ? h->d_partF : nullptr;
   a.part_theta = parity == 0 ? h->d_pthe : h->d_ptho;
   a.parity = parity;
   return a;
@@ -425,6 +432,8 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   a.part_th_odd = h->d_ptho;
   a.part_blk = h->d_part_blk;
   a.blocks_per_unit = h->fin_blocks;
+  a.pending = h->d_pending;
+  a.unit_sumTh_odd = h->d_usTo;
   a.unit_sumF = h->d_usF;
   a.unit_sumTh = h->d_usT;
   a.unit_F = h->d_uF;
@@ -451,18 +460,24 @@ int enqueue_measure_all(gf_handle* h, int mode) {
   return GF_OK;
 }
 
-// One sweep of the device-driven loop (four launches).  Consecutive passes over the
-// links walk the tiles in opposite directions, so each pass starts on the lines the
-// previous one left in L2; `pass` counts the passes (3 per sweep).
+// One sweep of the device-driven loop (five launches): even half-sweep, odd half-sweep
+// (F and odd-site theta fused on check sweeps), FINISH_ODD (which units the odd part
+// alone cannot decide), the even-site theta pass for those units (a no-op when there
+// are none), FINISH_LOOP.  Consecutive half-sweeps walk the tiles in opposite
+// directions, so each starts on the lines the previous one left in L2; the even-site
+// pass walks against the odd half-sweep.  `pass` counts half-sweeps (2 per sweep).
 int enqueue_loop_sweep(gf_handle* h, cudaStream_t s, int* pass) {
   const int st = cur_storage(h);
   launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 0, true, (*pass)++ & 1), h->n_tiles,
                h->threads, s);
   GF_CK_LAUNCH(h);
-  launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 1, true, (*pass)++ & 1), h->n_tiles,
+  const int rev_odd = (*pass)++ & 1;
+  launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 1, true, rev_odd), h->n_tiles,
                h->threads, s);
   GF_CK_LAUNCH(h);
-  launch_measure(st, h->nd, h->variant, measure_args(h, 0, true, (*pass)++ & 1), h->n_tiles, h->threads, s);
+  launch_finish(finish_args(h, FINISH_ODD), s);
+  GF_CK_LAUNCH(h);
+  launch_measure(st, h->nd, h->variant, measure_args(h, 0, true, rev_odd ^ 1), h->n_tiles, h->threads, s);
   GF_CK_LAUNCH(h);
   launch_finish(finish_args(h, FINISH_LOOP), s);
   GF_CK_LAUNCH(h);
@@ -472,7 +487,7 @@ int enqueue_loop_sweep(gf_handle* h, cudaStream_t s, int* pass) {
 int ensure_graph(gf_handle* h) {
   if (h->graph[h->cur]) return GF_OK;
   GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = GF_OK, pass = 0;  // kGraphSweeps * 3 passes: even, so replays keep alternating
+  int rc = GF_OK, pass = 0;  // kGraphSweeps * 2 half-sweeps: even, so replays keep alternating
   for (int j = 0; j < kGraphSweeps && rc == GF_OK; ++j) rc = enqueue_loop_sweep(h, h->cap_stream, &pass);
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
@@ -702,6 +717,10 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   h->d_pthe = (double*)(w + L.pthe);
   h->d_ptho = (double*)(w + L.ptho);
   h->d_part_blk = (double*)(w + L.part_blk);
+  h->d_pending = (int*)(w + L.pending);
+  h->d_usTo = (double*)(w + L.usTo);
+  if (cudaMemsetAsync(h->d_pending, 0, sizeof(int) * L.n_units, h->stream) != cudaSuccess)
+    return bail(GF_ECUDA, "initialisation of the pending masks failed");
   h->d_usF = (double*)(w + L.usF);
   h->d_usT = (double*)(w + L.usT);
   h->d_uF = (double*)(w + L.uF);
@@ -796,6 +815,20 @@ const char* gf_last_error(const gf_handle* h) { return h ? h->err.c_str() : g_cr
 int gf_num_lattices(const gf_handle* h) { return h ? h->n_lat : GF_EINVAL; }
 int gf_num_units(const gf_handle* h) { return h ? h->n_units : GF_EINVAL; }
 
+// Device address of host memory that kernels may access directly (pinned with
+// cudaHostAlloc or registered, and mapped into the device's address space); nullptr for
+// pageable memory, which then goes through the staging buffer.
+const double* host_mapped(const double* p) {
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of a pointer CUDA does not know
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr) return nullptr;
+  if (((uintptr_t)at.devicePointer % 16) != 0) return nullptr;
+  return static_cast<const double*>(at.devicePointer);
+}
+
 int gf_upload(gf_handle* h, int lat, const double* links, int on_device) {
   if (!h) return GF_EINVAL;
   if (lat < 0 || lat >= h->n_lat || !links) return fail(h, GF_EINVAL, "bad lattice index or null buffer");
@@ -803,8 +836,10 @@ int gf_upload(gf_handle* h, int lat, const double* links, int on_device) {
   h->cur = 0;
   h->sweeps_done = 0;
   const LatDev& d = h->lats[lat];
-  if (on_device) {
-    launch_pack(h->storage, h->links, d, links, 0, d.V, h->stream);
+  const double* mapped = on_device ? nullptr : host_mapped(links);
+  if (on_device || mapped) {
+    // device memory, or pinned host memory the kernel reads directly over the host link
+    launch_pack(h->storage, h->links, d, on_device ? links : mapped, 0, d.V, h->stream);
     GF_CK_LAUNCH(h);
   } else {
     const long long per = (long long)(h->L.staging_bytes / (4 * 144));
@@ -828,9 +863,11 @@ int gf_download(gf_handle* h, int lat, double* links, int on_device) {
   if (on_device && ((uintptr_t)links % 16) != 0) return fail(h, GF_EINVAL, "device buffer must be 16-byte aligned");
   const LatDev& d = cur_lat_host(h, lat);
   const int st = cur_storage(h);
-  if (on_device) {
-    launch_unpack(st, cur_links(h), d, links, 0, d.V, h->stream);
+  double* mapped = on_device ? nullptr : const_cast<double*>(host_mapped(links));
+  if (on_device || mapped) {
+    launch_unpack(st, cur_links(h), d, on_device ? links : mapped, 0, d.V, h->stream);
     GF_CK_LAUNCH(h);
+    if (mapped) GF_CK(h, cudaStreamSynchronize(h->stream));
   } else {
     const long long per = (long long)(h->L.staging_bytes / (4 * 144));
     for (long long s0 = 0; s0 < d.V; s0 += per) {

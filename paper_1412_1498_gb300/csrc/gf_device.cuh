@@ -60,6 +60,7 @@ struct DevState {
   int n_active;         // active units after the last check
   unsigned int ticket;  // last-block-done counter of the finishing kernel
   int stop;             // Fourier-accelerated loop: final field measured, nothing left to do
+  int need_exact;       // this check sweep has units whose odd-site theta alone is below eps
   double eps;           // stop threshold of the current phase
 };
 

@@ -6,9 +6,18 @@ namespace gf {
 // Two stages.  Block (u, j) adds tiles [j * kFinishThreads, (j + 1) * kFinishThreads) of
 // unit u with a fixed binary tree in shared memory (FP64 issues at ~1/64 of the FP32
 // rate here, so the tree does n - 1 additions instead of a shuffle tree's 5 n) and
-// stores the three sums.  The last block to take a ticket adds each unit's block sums
-// in order and finishes the unit (values, mask, iteration count), then the lattice
-// totals and the loop state.  The order of every addition is fixed: deterministic.
+// stores the sums.  The last block to take a ticket adds each unit's block sums in
+// order and finishes the units, then the lattice totals and the loop state.  The order
+// of every addition is fixed: deterministic.
+//
+// Modes.  MEASURE / RESET (outside the loop): F and theta of every unit from the two
+// parity passes; RESET also sets the masks.  In the loop a check sweep runs ODD after
+// the odd half-sweep, which measured F and the odd-site part of theta: theta >= the
+// odd part (every Tr[Delta Delta^+] >= 0), so a unit whose odd part is already >= eps
+// continues, exactly as the full theta would decide; the others (and every unit on the
+// last sweep of the budget) are marked pending.  The even-site pass then runs for the
+// pending units only, and LOOP completes their theta and masks, counts the sweep and
+// updates the loop state.
 __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   __shared__ double red[3][kFinishThreads];
   __shared__ int s_last;
@@ -16,19 +25,24 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   const int tid = (int)threadIdx.x;
   const int S = a.blocks_per_unit;
   const int u = (int)blockIdx.x / S, j = (int)blockIdx.x - u * S;
-  const bool loop = a.mode == FINISH_LOOP;
+  const bool loop = a.mode == FINISH_LOOP || a.mode == FINISH_ODD;
   bool check = true;
   if (loop) {
     if (!state_running(a.st)) return;  // uniform over the grid: nobody takes a ticket
     check = state_check_sweep(a.st);
+    if (a.mode == FINISH_ODD && !check) return;
   }
-  const bool reduce = loop ? (a.active[u] != 0 && check) : true;
+  bool reduce;
+  if (a.mode == FINISH_ODD) reduce = a.active[u] != 0;
+  else if (a.mode == FINISH_LOOP) reduce = check && a.active[u] != 0 && a.pending[u] != 0;
+  else reduce = true;
   if (reduce) {
     const int i = a.unit_tiles[u] + j * kFinishThreads + tid;
     const bool in = i < a.unit_tiles[u + 1];
-    red[0][tid] = in ? a.part_F[i] : 0.0;
-    red[1][tid] = in ? a.part_th_even[i] : 0.0;
-    red[2][tid] = in ? a.part_th_odd[i] : 0.0;
+    const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET;
+    red[0][tid] = in && a.mode != FINISH_LOOP ? a.part_F[i] : 0.0;
+    red[1][tid] = in ? (a.mode == FINISH_ODD ? a.part_th_odd[i] : a.part_th_even[i]) : 0.0;
+    red[2][tid] = in && outside ? a.part_th_odd[i] : 0.0;
     __syncthreads();
 #pragma unroll
     for (int w = kFinishThreads / 2; w > 0; w >>= 1) {
@@ -51,28 +65,62 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   if (!s_last) return;
   __threadfence();
   // last block: every unit from its block sums, in order
+  int cnt = 0;
+  const double eps = a.st->eps;
+  const bool forced = loop && a.st->sweep + 1 == a.st->limit;  // last sweep: measure exactly
   for (int v = tid; v < a.n_units; v += blockDim.x) {
     const bool was_active = __ldcg(a.active + v) != 0;
-    if (loop ? (was_active && check) : true) {
+    bool red_v;
+    if (a.mode == FINISH_ODD) red_v = was_active;
+    else if (a.mode == FINISH_LOOP) red_v = check && was_active && __ldcg(a.pending + v) != 0;
+    else red_v = true;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    if (red_v) {
       const int nb = (a.unit_tiles[v + 1] - a.unit_tiles[v] + kFinishThreads - 1) / kFinishThreads;
-      double sF = 0.0, sE = 0.0, sO = 0.0;
       for (int b = 0; b < nb; ++b) {
         const double* p = a.part_blk + 3 * (v * S + b);
-        sF += __ldcg(p);
-        sE += __ldcg(p + 1);
-        sO += __ldcg(p + 2);
+        s0 += __ldcg(p);
+        s1 += __ldcg(p + 1);
+        s2 += __ldcg(p + 2);
       }
-      const LatDev lat = a.lats[a.unit_lat[v]];
-      const double vol = a.nd == 4 ? (double)lat.V : 2.0 * lat.V3h;  // Landau: V, Coulomb: slice
-      const double sTh = sE + sO;
-      a.unit_sumF[v] = sF;
-      a.unit_sumTh[v] = sTh;
-      a.unit_F[v] = sF / ((double)a.nd * 3.0 * vol);
-      a.unit_theta[v] = sTh / (3.0 * vol);
-      // the loop reduces active units on check sweeps only; RESET re-derives every mask
-      if (loop || a.mode == FINISH_RESET) a.active[v] = sTh / (3.0 * vol) >= a.st->eps;
     }
-    if (loop && was_active) a.iters[v] += 1;
+    const LatDev lat = a.lats[a.unit_lat[v]];
+    const double vol = a.nd == 4 ? (double)lat.V : 2.0 * lat.V3h;  // Landau: V, Coulomb: slice
+    if (a.mode == FINISH_ODD) {
+      int pend = 0;
+      if (red_v) {
+        a.unit_sumF[v] = s0;
+        a.unit_F[v] = s0 / ((double)a.nd * 3.0 * vol);
+        a.unit_sumTh_odd[v] = s1;
+        pend = forced || !(s1 / (3.0 * vol) >= eps);
+      }
+      a.pending[v] = pend;
+      cnt += pend;
+    } else {
+      if (red_v) {
+        const double sTh = a.mode == FINISH_LOOP ? s1 + __ldcg(a.unit_sumTh_odd + v) : s1 + s2;
+        a.unit_sumTh[v] = sTh;
+        a.unit_theta[v] = sTh / (3.0 * vol);
+        if (a.mode != FINISH_LOOP) {
+          a.unit_sumF[v] = s0;
+          a.unit_F[v] = s0 / ((double)a.nd * 3.0 * vol);
+        }
+        if (a.mode != FINISH_MEASURE) a.active[v] = sTh / (3.0 * vol) >= eps;
+      }
+      if (a.mode == FINISH_LOOP && was_active) a.iters[v] += 1;
+    }
+  }
+  if (a.mode == FINISH_ODD) {
+    cnt = __reduce_add_sync(0xffffffffu, cnt);
+    if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+      int n = 0;
+      for (int w = 0; w < kFinishThreads / 32; ++w) n += s_cnt[w];
+      a.st->need_exact = n > 0;
+      a.st->ticket = 0u;
+    }
+    return;
   }
   __syncthreads();
   // lattice totals in a fixed order, active count, loop state
@@ -109,55 +157,72 @@ void launch_finish(const FinishArgs& a, cudaStream_t s) {
 // ---------------------------------------------------------------------------------
 // element kernels
 // ---------------------------------------------------------------------------------
-template <int S>
-__global__ void __launch_bounds__(256) k_pack(char* links, LatDev lat, const double2* src,
-                                              long long s0, long long nsites) {
-  using St = Store<S>;
-  using T = typename St::T;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= nsites * 4) return;
-  const long long s = s0 + i / 4;
-  const int mu = (int)(i % 4);
-  long long r = s;
-  const int x = (int)(r % lat.L[0]); r /= lat.L[0];
-  const int y = (int)(r % lat.L[1]); r /= lat.L[1];
-  const int z = (int)(r % lat.L[2]);
-  const int t = (int)(r / lat.L[2]);
-  const int p = (x + y + z + t) & 1;
-  const int idx = p * lat.Vh + (int)(s >> 1);
-  cx<T> e[St::NE];
-#pragma unroll
-  for (int k = 0; k < St::NE; ++k) {
-    const double2 v = src[i * 9 + k];
-    e[k] = {(T)v.x, (T)v.y};
-  }
-  St::store(links + lat.off_bytes, lat.V, mu, idx, e);
+// Canonical <-> storage.  A block takes kPackLinks consecutive canonical links (9
+// complex128 each, site-major): the canonical side moves through shared memory with
+// consecutive threads on consecutive 16-byte words (coalesced, also when the canonical
+// buffer is pinned host memory read or written directly over the host link); each
+// thread then converts one link.
+constexpr int kPackLinks = 128;
+
+__device__ __forceinline__ int storage_idx(const LatDev& lat, long long s) {
+  const int sl = (int)s;  // V < 2^31 (checked at creation)
+  const int x = sl % lat.L[0];
+  int r = sl / lat.L[0];
+  const int y = r % lat.L[1];
+  r /= lat.L[1];
+  const int z = r % lat.L[2];
+  const int t = r / lat.L[2];
+  return ((x + y + z + t) & 1) * lat.Vh + (sl >> 1);
 }
 
 template <int S>
-__global__ void __launch_bounds__(256) k_unpack(const char* links, LatDev lat, double2* dst,
-                                                long long s0, long long nsites) {
+__global__ void __launch_bounds__(kPackLinks) k_pack(char* links, LatDev lat, const double2* src,
+                                                     long long s0, long long nsites) {
   using St = Store<S>;
   using T = typename St::T;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= nsites * 4) return;
+  __shared__ double2 sm[kPackLinks * 9];
+  const long long l0 = (long long)blockIdx.x * kPackLinks;  // first link of the block
+  const long long nl = nsites * 4;
+  const int nb = (int)(nl - l0 < kPackLinks ? nl - l0 : kPackLinks);
+  for (int w = threadIdx.x; w < nb * 9; w += kPackLinks) sm[w] = src[l0 * 9 + w];
+  __syncthreads();
+  if ((int)threadIdx.x >= nb) return;
+  const long long i = l0 + threadIdx.x;
   const long long s = s0 + i / 4;
   const int mu = (int)(i % 4);
-  long long r = s;
-  const int x = (int)(r % lat.L[0]); r /= lat.L[0];
-  const int y = (int)(r % lat.L[1]); r /= lat.L[1];
-  const int z = (int)(r % lat.L[2]);
-  const int t = (int)(r / lat.L[2]);
-  const int p = (x + y + z + t) & 1;
-  const int idx = p * lat.Vh + (int)(s >> 1);
   cx<T> e[St::NE];
-  St::load(links + lat.off_bytes, lat.V, mu, idx, e);
-  cx<double> m[9];
 #pragma unroll
-  for (int k = 0; k < St::NE; ++k) m[k] = {(double)e[k].re, (double)e[k].im};
-  if constexpr (St::NE == 6) third_row(m, m + 6);
+  for (int k = 0; k < St::NE; ++k) {
+    const double2 v = sm[threadIdx.x * 9 + k];
+    e[k] = {(T)v.x, (T)v.y};
+  }
+  St::store(links + lat.off_bytes, lat.V, mu, storage_idx(lat, s), e);
+}
+
+template <int S>
+__global__ void __launch_bounds__(kPackLinks) k_unpack(const char* links, LatDev lat, double2* dst,
+                                                       long long s0, long long nsites) {
+  using St = Store<S>;
+  using T = typename St::T;
+  __shared__ double2 sm[kPackLinks * 9];
+  const long long l0 = (long long)blockIdx.x * kPackLinks;
+  const long long nl = nsites * 4;
+  const int nb = (int)(nl - l0 < kPackLinks ? nl - l0 : kPackLinks);
+  if ((int)threadIdx.x < nb) {
+    const long long i = l0 + threadIdx.x;
+    const long long s = s0 + i / 4;
+    const int mu = (int)(i % 4);
+    cx<T> e[St::NE];
+    St::load(links + lat.off_bytes, lat.V, mu, storage_idx(lat, s), e);
+    cx<double> m[9];
 #pragma unroll
-  for (int k = 0; k < 9; ++k) dst[i * 9 + k] = make_double2(m[k].re, m[k].im);
+    for (int k = 0; k < St::NE; ++k) m[k] = {(double)e[k].re, (double)e[k].im};
+    if constexpr (St::NE == 6) third_row(m, m + 6);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) sm[threadIdx.x * 9 + k] = make_double2(m[k].re, m[k].im);
+  }
+  __syncthreads();
+  for (int w = threadIdx.x; w < nb * 9; w += kPackLinks) dst[l0 * 9 + w] = sm[w];
 }
 
 template <int S>
@@ -214,9 +279,9 @@ static unsigned int blocks_for(long long n, int threads) { return (unsigned int)
 void launch_pack(int storage, char* links, const LatDev& lat, const double* src, long long s0,
                  long long nsites, cudaStream_t s) {
   if (nsites <= 0) return;
-  const unsigned int nb = blocks_for(nsites * 4, 256);
+  const unsigned int nb = blocks_for(nsites * 4, kPackLinks);
   const double2* p = reinterpret_cast<const double2*>(src);
-#define GF_CALL(S) k_pack<S><<<nb, 256, 0, s>>>(links, lat, p, s0, nsites)
+#define GF_CALL(S) k_pack<S><<<nb, kPackLinks, 0, s>>>(links, lat, p, s0, nsites)
   GF_ELEM_SWITCH(storage, GF_CALL)
 #undef GF_CALL
 }
@@ -224,9 +289,9 @@ void launch_pack(int storage, char* links, const LatDev& lat, const double* src,
 void launch_unpack(int storage, const char* links, const LatDev& lat, double* dst, long long s0,
                    long long nsites, cudaStream_t s) {
   if (nsites <= 0) return;
-  const unsigned int nb = blocks_for(nsites * 4, 256);
+  const unsigned int nb = blocks_for(nsites * 4, kPackLinks);
   double2* p = reinterpret_cast<double2*>(dst);
-#define GF_CALL(S) k_unpack<S><<<nb, 256, 0, s>>>(links, lat, p, s0, nsites)
+#define GF_CALL(S) k_unpack<S><<<nb, kPackLinks, 0, s>>>(links, lat, p, s0, nsites)
   GF_ELEM_SWITCH(storage, GF_CALL)
 #undef GF_CALL
 }

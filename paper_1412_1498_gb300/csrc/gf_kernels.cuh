@@ -176,6 +176,7 @@ struct SweepArgs {
   const int* active;       // per unit (nullable: all active)
   const DevState* st;      // nullable; when set, the loop state decides everything
   double* part_theta;      // per tile: theta partial of the updated (odd) sites
+  double* part_F;          // nullable; per tile: Re Tr of the updated sites' 2 nd links
   int parity;
   int form;
   int reunit;              // used when st == nullptr
@@ -205,6 +206,8 @@ struct FinishArgs {
   const int* unit_tiles;   // n_units + 1 tile boundaries
   double* part_blk;        // 3 sums per finishing block
   int blocks_per_unit;     // finishing blocks per unit: ceil(max tiles of a unit / kFinishThreads)
+  int* pending;            // per unit: this check needs the even-site pass (FINISH_ODD sets it)
+  double* unit_sumTh_odd;  // per unit: odd-site part of the theta sum of the current check
   const int* unit_lat;     // lattice of each unit
   int* active;
   int* iters;
@@ -224,7 +227,7 @@ struct FinishArgs {
   int mode;                // FINISH_LOOP, FINISH_MEASURE, FINISH_RESET
 };
 
-enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2 };
+enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2, FINISH_ODD = 3 };
 
 // Fourier-accelerated steepest descent (kernels in gf_fasd.cuh)
 struct FasdArgs {
@@ -279,7 +282,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   using T = typename St::T;
   constexpr int NE = St::NE;
   constexpr bool KEEP = sizeof(T) == 4;
-  __shared__ double red[32];
+  __shared__ double red[64];
 
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
@@ -292,7 +295,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   if (a.active && !a.active[tile.w]) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
-  T q = T(0);
+  T q = T(0), fs = T(0);
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
@@ -330,7 +333,10 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
           reunit(f[mu]);
           reunit(b[mu]);
         }
-        if (mu < ND && measure_now) add_to_A(A, f[mu], b[mu]);
+        if (mu < ND && measure_now) {
+          add_to_A(A, f[mu], b[mu]);
+          fs = fs + (re_trace(f[mu]) + re_trace(b[mu]));
+        }
         St::store(base, V, mu, idx_f, f[mu]);
         St::store(base, V, mu, idx_b[mu], b[mu]);
       }
@@ -358,7 +364,10 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
           reunit(f);
           reunit(b);
         }
-        if (mu < ND && measure_now) add_to_A(A, f, b);
+        if (mu < ND && measure_now) {
+          add_to_A(A, f, b);
+          fs = fs + (re_trace(f) + re_trace(b));
+        }
         St::store(base, V, mu, idx_f, f);
         St::store(base, V, mu, idx_b[mu], b);
       }
@@ -366,10 +375,13 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
     }
   }
   if (measure_now) {
-    const T v[1] = {q};
-    double o[1];
-    tile_sum<T, 1>(v, o, red);
-    if (threadIdx.x == 0) a.part_theta[ti] = o[0];
+    const T v[2] = {fs, q};
+    double o[2];
+    tile_sum<T, 2>(v, o, red);
+    if (threadIdx.x == 0) {
+      if (a.part_F) a.part_F[ti] = o[0];
+      a.part_theta[ti] = o[1];
+    }
   }
 }
 
@@ -384,7 +396,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   using T = typename St::T;
   constexpr int NE = St::NE;
   __shared__ double red[64];
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st))) return;
+  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
   if (a.active && !a.active[tile.w]) return;

@@ -229,7 +229,7 @@ __device__ __forceinline__ float split_theta_site(const acc2 (&A)[18]) {
 // ------------------------------------------------------------------------- the sweep
 template <int ND>
 __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
-  __shared__ double red[32];
+  __shared__ double red[64];
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
     if (!state_running(a.st)) return;
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
   if (a.active && !a.active[tile.w]) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
-  float q = 0.f;
+  float q = 0.f, fsum = 0.f;
   if (h3 < lat.V3h) {
     const int p = a.parity;
     const int h = tile.y * lat.V3h + h3;
@@ -327,6 +327,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
     for (int mu = 0; mu < 4; ++mu) {
       // forward link: U_mu(x) += E U_mu(x); then backward: U_mu(x-mu) += U_mu(x-mu) E^+
       // (one split link live at a time)
+      float tr[2] = {0.f, 0.f};
 #pragma unroll 1
       for (int side = 0; side < 2; ++side) {
         const int idx = side == 0 ? idx_f : idx_b[mu];
@@ -355,17 +356,22 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
             acc_add(A[2 * e], sg * u[e].re.hi, sg * u[e].re.lo);
             acc_add(A[2 * e + 1], sg * u[e].im.hi, sg * u[e].im.lo);
           }
+          tr[side] = sf_f(u[0].re) + sf_f(u[4].re) + sf_f(u[8].re);
         }
         split_store(base, V, mu, idx, u);
       }
+      if (mu < ND && measure_now) fsum = fsum + (tr[0] + tr[1]);
     }
     if (measure_now) q = split_theta_site(A);
   }
   if (measure_now) {
-    const float v[1] = {q};
-    double o[1];
-    block_sum_f32<1>(v, o, reinterpret_cast<float*>(red));
-    if (threadIdx.x == 0) a.part_theta[ti] = o[0];
+    const float v[2] = {fsum, q};
+    double o[2];
+    block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
+    if (threadIdx.x == 0) {
+      if (a.part_F) a.part_F[ti] = o[0];
+      a.part_theta[ti] = o[1];
+    }
   }
 }
 
@@ -373,7 +379,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
 template <int ND>
 __global__ void __launch_bounds__(128) k_measure_split(MeasureArgs a) {
   __shared__ double red[64];
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st))) return;
+  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
   if (a.active && !a.active[tile.w]) return;

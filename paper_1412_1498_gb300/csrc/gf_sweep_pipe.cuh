@@ -78,7 +78,7 @@ __device__ __forceinline__ void pipe_read(const float4* slot, int B, int word0, 
 template <int ND>
 __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
   extern __shared__ float4 sm[];
-  __shared__ double red[32];
+  __shared__ double red[64];
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
     if (!state_running(a.st)) return;
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
     cp_async_commit();
     cp_async_wait_all_but_newest();  // this thread's copies of tile k have landed
     if (cur.active) {
-      float q = 0.f;
+      float q = 0.f, fs = 0.f;
       if (cur.valid) {
         const LatDev lat = a.lats[cur.lat];
         float4* g = reinterpret_cast<float4*>(a.links + lat.off_bytes);
@@ -129,7 +129,10 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
             reunit(f);
             reunit(b);
           }
-          if (mu < ND && measure_now) add_to_A(A, f, b);
+          if (mu < ND && measure_now) {
+            add_to_A(A, f, b);
+            fs = fs + (re_trace(f) + re_trace(b));
+          }
 #pragma unroll
           for (int w = 0; w < 3; ++w) {
             g[(long long)(w * 4 + mu) * lat.V + cur.idx_f] =
@@ -141,10 +144,13 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
         if (measure_now) q = theta_site(A);
       }
       if (measure_now) {
-        const float v[1] = {q};
-        double o[1];
-        block_sum_f32<1>(v, o, reinterpret_cast<float*>(red));
-        if (threadIdx.x == 0) a.part_theta[cur.ti] = o[0];
+        const float v[2] = {fs, q};
+        double o[2];
+        block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
+        if (threadIdx.x == 0) {
+          if (a.part_F) a.part_F[cur.ti] = o[0];
+          a.part_theta[cur.ti] = o[1];
+        }
         __syncthreads();  // red[] is reused by the next tile
       }
     }
@@ -200,7 +206,7 @@ template <int ND>
 __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
   extern __shared__ float4 sm[];
   __shared__ double red[64];
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st))) return;
+  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
   int k = blockIdx.x;
   if (k >= a.n_tiles) return;
   const int B = blockDim.x;

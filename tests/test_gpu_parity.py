@@ -45,10 +45,12 @@ def nd_of(gauge):
 
 
 # ---------------------------------------------------------------- layout conversion
+@pytest.mark.parametrize("dims", [DIMS, (6, 2, 2, 2)])
 @pytest.mark.parametrize("storage", [0, 1, 2])
-def test_upload_download_roundtrip(gf, storage):
-    U = fields.random_gauge_config(DIMS, 0.5, 41)
-    fx = make(gf, DIMS, gf.GF_LANDAU, storage)
+def test_upload_download_roundtrip(gf, storage, dims):
+    # (6, 2, 2, 2): 192 links, a ragged second block of the 128-link conversion kernels
+    U = fields.random_gauge_config(dims, 0.5, 41)
+    fx = make(gf, dims, gf.GF_LANDAU, storage)
     fx.upload(U)
     got = fx.download()
     if storage == gf.GF_FP64_18:
@@ -67,6 +69,12 @@ def test_upload_download_roundtrip(gf, storage):
     fx.download(out=outd)
     torch.cuda.synchronize()
     assert np.array_equal(outd.cpu().numpy(), got)
+    # pinned host buffers: the conversion kernels read and write them directly
+    Up = torch.from_numpy(U).pin_memory()
+    fx.upload(Up)
+    outp = torch.zeros_like(Up).pin_memory()
+    fx.download(out=outp)
+    assert np.array_equal(outp.numpy(), got)
     fx.close()
 
 
@@ -157,6 +165,39 @@ def test_fix_matches_oracle_run(gf, gauge):
     assert np.array_equal(got, ref)
     assert abs(out["F"][0] - r["F"]) <= 1e-12 * abs(r["F"])
     assert abs(out["theta"][0] - r["theta"]) <= 1e-12 * r["theta"]
+    fx.close()
+
+
+@pytest.mark.parametrize("k", [1, 7])
+def test_stop_rule_with_check_interval(gf, k):
+    # The loop measures F and the odd-site part of theta in the odd half-sweep and runs
+    # the even-site pass only when that part alone is below eps (theta >= its odd part),
+    # and on the last sweep of the budget.  The stop sweep must be the first checked
+    # sweep with theta < eps in the oracle's history, with the oracle's field and values.
+    dims = (8, 8, 8, 8)
+    U = fields.random_gauge_config(dims, 0.4, 1, 2)
+    eps = 1e-12
+    r = oracle.fix(U.copy(), 1e-300, 500, 1.7)
+    hist = r["theta_hist"]                       # before the loop, then after every sweep
+    expected = next(n for n in range(1, len(hist)) if n % k == 0 and hist[n] < eps)
+    fx = make(gf, dims, gf.GF_LANDAU, gf.GF_FP64_18, repro=True)
+    gf.gf_set_check_interval(fx.h, k)
+    fx.upload(U)
+    out = fx.fix(eps, 500)
+    assert out["rc"] == gf.GF_OK and out["iters"][0] == expected
+    ref = U.copy()
+    rr = oracle.fix(ref, 1e-300, expected, 1.7)
+    assert np.array_equal(fx.download(), ref)
+    assert abs(out["theta"][0] - rr["theta"]) <= 1e-12 * rr["theta"]
+    assert abs(out["F"][0] - rr["F"]) <= 1e-12 * abs(rr["F"])
+    # budget end between checks: the last sweep is measured exactly
+    fx.upload(U)
+    out = fx.fix(1e-300, 7)
+    ref = U.copy()
+    rr = oracle.fix(ref, 1e-300, 7, 1.7)
+    assert out["iters"][0] == 7 and out["rc"] == gf.GF_ENOTCONVERGED
+    assert abs(out["theta"][0] - rr["theta"]) <= 1e-12 * rr["theta"]
+    assert abs(out["F"][0] - rr["F"]) <= 1e-12 * abs(rr["F"])
     fx.close()
 
 
