@@ -122,7 +122,7 @@ int link_bytes(int storage) {
 
 struct Layout {
   size_t links, links64, staging, lats, lats64, tiles, unit_tiles, unit_lat, active, iters, partF,
-      pthe, ptho, part_blk, pending, usTo, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
+      pthe, ptho, part_blk, pending, usTo, unit_vol, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
       unit_planes, ad_g, ad_delta, ad_part, ad_ticket, total;
   size_t staging_bytes;
   int max_tiles, n_units;
@@ -181,6 +181,7 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->part_blk = take(sizeof(double) * 3 * (size_t)n_units * fin_blocks);
   L->pending = take(sizeof(int) * n_units);
   L->usTo = take(sizeof(double) * n_units);
+  L->unit_vol = take(sizeof(double) * n_units);
   L->usF = take(sizeof(double) * n_units);
   L->usT = take(sizeof(double) * n_units);
   L->uF = take(sizeof(double) * n_units);
@@ -281,6 +282,7 @@ struct gf_handle {
   double *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr, *d_part_blk = nullptr,
          *d_usTo = nullptr;
   int* d_pending = nullptr;
+  double* d_unit_vol = nullptr;
   int fin_blocks = 1;  // finishing blocks per unit for the current tile table
   double *d_usF = nullptr, *d_usT = nullptr, *d_uF = nullptr, *d_uT = nullptr, *d_lF = nullptr,
          *d_lT = nullptr;
@@ -379,6 +381,13 @@ int build_tiles(gf_handle* h) {
                            cudaMemcpyHostToDevice, h->stream));
   GF_CK(h, cudaMemcpyAsync(h->d_unit_lat, unit_lat.data(), sizeof(int) * unit_lat.size(),
                            cudaMemcpyHostToDevice, h->stream));
+  std::vector<double> unit_vol;
+  for (int l : unit_lat) {
+    const LatDev& lat = h->lats[l];
+    unit_vol.push_back(h->gauge == GF_LANDAU ? (double)lat.V : 2.0 * lat.V3h);
+  }
+  GF_CK(h, cudaMemcpyAsync(h->d_unit_vol, unit_vol.data(), sizeof(double) * unit_vol.size(),
+                           cudaMemcpyHostToDevice, h->stream));
   GF_CK(h, cudaStreamSynchronize(h->stream));  // host vectors die on return
   drop_graphs(h);
   return GF_OK;
@@ -425,6 +434,7 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   a.lats = cur_lats(h);
   a.unit_tiles = h->d_unit_tiles;
   a.unit_lat = h->d_unit_lat;
+  a.unit_vol = h->d_unit_vol;
   a.active = h->d_active;
   a.iters = h->d_iters;
   a.part_F = h->d_partF;
@@ -719,6 +729,7 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   h->d_part_blk = (double*)(w + L.part_blk);
   h->d_pending = (int*)(w + L.pending);
   h->d_usTo = (double*)(w + L.usTo);
+  h->d_unit_vol = (double*)(w + L.unit_vol);
   if (cudaMemsetAsync(h->d_pending, 0, sizeof(int) * L.n_units, h->stream) != cudaSuccess)
     return bail(GF_ECUDA, "initialisation of the pending masks failed");
   h->d_usF = (double*)(w + L.usF);

@@ -61,6 +61,7 @@ struct DevState {
   unsigned int ticket;  // last-block-done counter of the finishing kernel
   int stop;             // Fourier-accelerated loop: final field measured, nothing left to do
   int need_exact;       // this check sweep has units whose odd-site theta alone is below eps
+  int sweep_closed;     // the odd-part finish already counted this sweep (nothing pending)
   double eps;           // stop threshold of the current phase
 };
 

@@ -93,14 +93,6 @@ __device__ __forceinline__ long long fwd_lexi(const LatDev& lat, const Site& s, 
     default: return s.t == lat.L[3] - 1 ? s.lexi - V3 * (lat.L[3] - 1) : s.lexi + V3;
   }
 }
-__device__ __forceinline__ int idx_of_lexi(const LatDev& lat, long long lexi) {
-  long long r = lexi;
-  const int x = (int)(r % lat.L[0]); r /= lat.L[0];
-  const int y = (int)(r % lat.L[1]); r /= lat.L[1];
-  const int z = (int)(r % lat.L[2]);
-  const int t = (int)(r / lat.L[2]);
-  return ((x + y + z + t) & 1) * lat.Vh + (int)(lexi >> 1);
-}
 __device__ __forceinline__ bool fasd_running(const DevState* st) {
   return st == nullptr || (st->n_active > 0 && st->sweep < st->limit);
 }
@@ -157,11 +149,12 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
   twiddles(twy, a.logL[1]);
   T fsum = T(0), q = T(0);
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    const int x = i % Lx, y = i / Lx;
+    const int x = i & (Lx - 1), y = i >> a.logL[0];  // Lx, Ly are powers of 2 here
     Site s;
     s.x = x; s.y = y; s.z = z; s.t = t;
     s.lexi = x + (long long)Lx * (y + (long long)Ly * (z + (long long)lat.L[2] * t));
-    const int idx = ((x + y + z + t) & 1) * lat.Vh + (int)(s.lexi >> 1);
+    const int p = (x + y + z + t) & 1;
+    const int idx = p * lat.Vh + (int)(s.lexi >> 1);
     const char* base = a.links + lat.off_bytes;
     cx<T> A[9];
 #pragma unroll
@@ -170,7 +163,8 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
     for (int nu = 0; nu < ND; ++nu) {
       cx<T> f[NE], b[NE];
       St::load(base, lat.V, nu, idx, f);
-      St::load(base, lat.V, nu, idx_of_lexi(lat, back_lexi(lat, s, nu)), b);
+      // all extents are even, so x - nu has the other parity
+      St::load(base, lat.V, nu, (1 - p) * lat.Vh + (int)(back_lexi(lat, s, nu) >> 1), b);
       fsum = fsum + re_trace(f);   // forward links only: every link once over all sites
       add_to_A(A, f, b);
     }
@@ -209,7 +203,7 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
   const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
 #pragma unroll 8
   for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
-    const int f = i / P, j = i % P;
+    const int f = i >> (a.logL[0] + a.logL[1]), j = i & (P - 1);
     kb[f * lat.V + plane0 + j] = pl[i];
   }
 }
@@ -355,12 +349,13 @@ __global__ void __launch_bounds__(256) k_fasd_xy_inv_g(FasdArgs a) {
   const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf);
   const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
 #pragma unroll 8
-  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) pl[i] = kb[(i / P) * lat.V + plane0 + i % P];
+  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x)
+    pl[i] = kb[(i >> (a.logL[0] + a.logL[1])) * lat.V + plane0 + (i & (P - 1))];
   __syncthreads();
   fft_lines(pl, twy, 4 * Lx, a.logL[1], Lx, 1, P, Lx, +1);
   fft_lines(pl, twx, 4 * Ly, a.logL[0], 1, 0, Lx, 1, +1);
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    const int x = i % Lx, y = i / Lx;
+    const int x = i & (Lx - 1), y = i >> a.logL[0];
     const long long lexi = x + (long long)Lx * (y + (long long)Ly * (z + (long long)lat.L[2] * t));
     const int idx = ((x + y + z + t) & 1) * lat.Vh + (int)(lexi >> 1);
     // Delta~ (already scaled by alpha/2 p^2_max/p^2/N): anti-Hermitian, traceless
@@ -410,7 +405,7 @@ __global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
     St::load(base, lat.V, mu, (int)i, u);
     if (act) left_mul(g, u);
     if (act_fwd) {
-      g_load<T>(a.gbuf, lat.V, idx_of_lexi(lat, fwd_lexi(lat, s, mu)), gn);
+      g_load<T>(a.gbuf, lat.V, (1 - p) * lat.Vh + (int)(fwd_lexi(lat, s, mu) >> 1), gn);
       right_mul_dag(u, gn);
     }
     if (reunit_now) reunit(u);

@@ -30,7 +30,11 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   if (loop) {
     if (!state_running(a.st)) return;  // uniform over the grid: nobody takes a ticket
     check = state_check_sweep(a.st);
-    if (a.mode == FINISH_ODD && !check) return;
+    if (a.mode == FINISH_ODD && !check) {
+      if (blockIdx.x == 0 && tid == 0) a.st->sweep_closed = 0;
+      return;
+    }
+    if (a.mode == FINISH_LOOP && a.st->sweep_closed) return;  // written by the previous launch
   }
   bool reduce;
   if (a.mode == FINISH_ODD) reduce = a.active[u] != 0;
@@ -64,15 +68,23 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last block: every unit from its block sums, in order
-  int cnt = 0;
+  // last block: every unit from its block sums, in order.  All loads of a unit are
+  // independent of one another; per-unit results stay in shared memory for the lattice
+  // totals when the units fit, so the tail is one round of loads, then stores.
+  __shared__ double s_uF[kFinishThreads], s_uT[kFinishThreads];
+  const bool small = a.n_units <= kFinishThreads;
+  int cnt = 0;  // ODD: pending units; otherwise: active units after this step
   const double eps = a.st->eps;
   const bool forced = loop && a.st->sweep + 1 == a.st->limit;  // last sweep: measure exactly
   for (int v = tid; v < a.n_units; v += blockDim.x) {
     const bool was_active = __ldcg(a.active + v) != 0;
+    const bool pend_in = a.mode == FINISH_LOOP && __ldcg(a.pending + v) != 0;
+    const double vol = a.unit_vol[v];
+    double uF = __ldcg(a.unit_sumF + v), uT = __ldcg(a.unit_sumTh + v);
+    const double uTo = a.mode == FINISH_LOOP ? __ldcg(a.unit_sumTh_odd + v) : 0.0;
     bool red_v;
     if (a.mode == FINISH_ODD) red_v = was_active;
-    else if (a.mode == FINISH_LOOP) red_v = check && was_active && __ldcg(a.pending + v) != 0;
+    else if (a.mode == FINISH_LOOP) red_v = check && was_active && pend_in;
     else red_v = true;
     double s0 = 0.0, s1 = 0.0, s2 = 0.0;
     if (red_v) {
@@ -84,11 +96,11 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
         s2 += __ldcg(p + 2);
       }
     }
-    const LatDev lat = a.lats[a.unit_lat[v]];
-    const double vol = a.nd == 4 ? (double)lat.V : 2.0 * lat.V3h;  // Landau: V, Coulomb: slice
+    bool act = was_active;
     if (a.mode == FINISH_ODD) {
       int pend = 0;
       if (red_v) {
+        uF = s0;
         a.unit_sumF[v] = s0;
         a.unit_F[v] = s0 / ((double)a.nd * 3.0 * vol);
         a.unit_sumTh_odd[v] = s1;
@@ -98,52 +110,77 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
       cnt += pend;
     } else {
       if (red_v) {
-        const double sTh = a.mode == FINISH_LOOP ? s1 + __ldcg(a.unit_sumTh_odd + v) : s1 + s2;
-        a.unit_sumTh[v] = sTh;
-        a.unit_theta[v] = sTh / (3.0 * vol);
+        uT = a.mode == FINISH_LOOP ? s1 + uTo : s1 + s2;
+        a.unit_sumTh[v] = uT;
+        a.unit_theta[v] = uT / (3.0 * vol);
         if (a.mode != FINISH_LOOP) {
+          uF = s0;
           a.unit_sumF[v] = s0;
           a.unit_F[v] = s0 / ((double)a.nd * 3.0 * vol);
         }
-        if (a.mode != FINISH_MEASURE) a.active[v] = sTh / (3.0 * vol) >= eps;
+        if (a.mode != FINISH_MEASURE) {
+          act = uT / (3.0 * vol) >= eps;
+          a.active[v] = act;
+        }
       }
       if (a.mode == FINISH_LOOP && was_active) a.iters[v] += 1;
+      cnt += act;
+    }
+    if (small) {
+      s_uF[v] = uF;
+      s_uT[v] = uT;
     }
   }
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
+  __syncthreads();
+  int n = 0;
+  for (int w = 0; w < kFinishThreads / 32; ++w) n += s_cnt[w];
   if (a.mode == FINISH_ODD) {
-    cnt = __reduce_add_sync(0xffffffffu, cnt);
-    if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
-    __syncthreads();
+    if (n > 0) {
+      if (tid == 0) {
+        a.st->need_exact = 1;
+        a.st->sweep_closed = 0;
+        a.st->ticket = 0u;
+      }
+      return;
+    }
+    // nothing pending: every active unit continues, so the sweep's bookkeeping is done
+    // here and the even-site pass and FINISH_LOOP of this sweep do nothing
+    for (int v = tid; v < a.n_units; v += blockDim.x)
+      if (__ldcg(a.active + v) != 0) a.iters[v] += 1;
+    for (int l = tid; l < a.n_lat; l += blockDim.x) {
+      const LatDev lat = a.lats[l];
+      double sF = 0.0, sTh = 0.0;
+      for (int k = 0; k < lat.n_units; ++k) {
+        sF += small ? s_uF[lat.unit0 + k] : __ldcg(a.unit_sumF + lat.unit0 + k);
+        sTh += small ? s_uT[lat.unit0 + k] : __ldcg(a.unit_sumTh + lat.unit0 + k);
+      }
+      a.lat_F[l] = sF / ((double)a.nd * 3.0 * (double)lat.V);
+      a.lat_theta[l] = sTh / (3.0 * (double)lat.V);
+    }
     if (tid == 0) {
-      int n = 0;
-      for (int w = 0; w < kFinishThreads / 32; ++w) n += s_cnt[w];
-      a.st->need_exact = n > 0;
+      a.st->need_exact = 0;
+      a.st->sweep_closed = 1;
+      a.st->sweep += 1;
       a.st->ticket = 0u;
     }
     return;
   }
-  __syncthreads();
-  // lattice totals in a fixed order, active count, loop state
+  // lattice totals in a fixed order, loop state
   if (!loop || check) {
     for (int l = tid; l < a.n_lat; l += blockDim.x) {
       const LatDev lat = a.lats[l];
       double sF = 0.0, sTh = 0.0;
       for (int k = 0; k < lat.n_units; ++k) {
-        sF += __ldcg(a.unit_sumF + lat.unit0 + k);
-        sTh += __ldcg(a.unit_sumTh + lat.unit0 + k);
+        sF += small ? s_uF[lat.unit0 + k] : __ldcg(a.unit_sumF + lat.unit0 + k);
+        sTh += small ? s_uT[lat.unit0 + k] : __ldcg(a.unit_sumTh + lat.unit0 + k);
       }
       a.lat_F[l] = sF / ((double)a.nd * 3.0 * (double)lat.V);
       a.lat_theta[l] = sTh / (3.0 * (double)lat.V);
     }
   }
-  int c = 0;
-  for (int k = tid; k < a.n_units; k += blockDim.x) c += __ldcg(a.active + k);
-  c = __reduce_add_sync(0xffffffffu, c);
-  if ((tid & 31) == 0) s_cnt[tid >> 5] = c;
-  __syncthreads();
   if (tid == 0) {
-    int n = 0;
-    for (int w = 0; w < kFinishThreads / 32; ++w) n += s_cnt[w];
     if (a.mode != FINISH_MEASURE) a.st->n_active = n;
     if (loop) a.st->sweep += 1;
     a.st->ticket = 0u;

@@ -131,6 +131,18 @@ __device__ __forceinline__ void add_to_A(cx<T> (&A)[9], const cx<T> (&f)[NE], co
   for (int e = 0; e < 9; ++e) A[e] = cadd(A[e], csub(bu[e], fu[e]));
 }
 
+// add_to_A and F += Re Tr f + Re Tr b from the same full matrices (Re Tr of a 12-real
+// link is e0 + e4 + Re(e0 e4 - e1 e3), the (2,2) element of its rebuilt third row)
+template <class T, int NE>
+__device__ __forceinline__ void add_to_A_F(cx<T> (&A)[9], T& fs, const cx<T> (&f)[NE], const cx<T> (&b)[NE]) {
+  cx<T> fu[9], bu[9];
+  to_full(f, fu);
+  to_full(b, bu);
+#pragma unroll
+  for (int e = 0; e < 9; ++e) A[e] = cadd(A[e], csub(bu[e], fu[e]));
+  fs = fs + ((fu[0].re + fu[4].re + fu[8].re) + (bu[0].re + bu[4].re + bu[8].re));
+}
+
 // Tr[Delta Delta^dagger] with Delta = A - A^dagger - (1/3) Tr(A - A^dagger)
 template <class T>
 __device__ __forceinline__ T theta_site(const cx<T> (&A)[9]) {
@@ -209,6 +221,7 @@ struct FinishArgs {
   int* pending;            // per unit: this check needs the even-site pass (FINISH_ODD sets it)
   double* unit_sumTh_odd;  // per unit: odd-site part of the theta sum of the current check
   const int* unit_lat;     // lattice of each unit
+  const double* unit_vol;  // sites of each unit (Landau: V, Coulomb: Lx Ly Lz)
   int* active;
   int* iters;
   const double* part_F;
@@ -333,10 +346,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
           reunit(f[mu]);
           reunit(b[mu]);
         }
-        if (mu < ND && measure_now) {
-          add_to_A(A, f[mu], b[mu]);
-          fs = fs + (re_trace(f[mu]) + re_trace(b[mu]));
-        }
+        if (mu < ND && measure_now) add_to_A_F(A, fs, f[mu], b[mu]);
         St::store(base, V, mu, idx_f, f[mu]);
         St::store(base, V, mu, idx_b[mu], b[mu]);
       }
@@ -364,10 +374,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
           reunit(f);
           reunit(b);
         }
-        if (mu < ND && measure_now) {
-          add_to_A(A, f, b);
-          fs = fs + (re_trace(f) + re_trace(b));
-        }
+        if (mu < ND && measure_now) add_to_A_F(A, fs, f, b);
         St::store(base, V, mu, idx_f, f);
         St::store(base, V, mu, idx_b[mu], b);
       }
@@ -423,8 +430,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
       }
 #pragma unroll
       for (int nu = 0; nu < ND; ++nu) {
-        fs = fs + (re_trace(f[nu]) + re_trace(b[nu]));
-        add_to_A(A, f[nu], b[nu]);
+        add_to_A_F(A, fs, f[nu], b[nu]);
       }
     } else {
 #pragma unroll
@@ -432,8 +438,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
         cx<T> f[NE], b[NE];
         St::load(base, lat.V, nu, idx_f, f);
         St::load(base, lat.V, nu, (1 - p) * lat.Vh + (int)(back_lexi(lat, s, nu) >> 1), b);
-        fs = fs + (re_trace(f) + re_trace(b));
-        add_to_A(A, f, b);
+        add_to_A_F(A, fs, f, b);
       }
     }
     fsum = fs;

@@ -129,10 +129,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
             reunit(f);
             reunit(b);
           }
-          if (mu < ND && measure_now) {
-            add_to_A(A, f, b);
-            fs = fs + (re_trace(f) + re_trace(b));
-          }
+          if (mu < ND && measure_now) add_to_A_F(A, fs, f, b);
 #pragma unroll
           for (int w = 0; w < 3; ++w) {
             g[(long long)(w * 4 + mu) * lat.V + cur.idx_f] =
@@ -235,8 +232,7 @@ __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
         float fs = 0.f;
 #pragma unroll
         for (int nu = 0; nu < ND; ++nu) {
-          fs = fs + (re_trace(f[nu]) + re_trace(b[nu]));
-          add_to_A(A, f[nu], b[nu]);
+          add_to_A_F(A, fs, f[nu], b[nu]);
         }
         fsum = fs;
         q = theta_site(A);
