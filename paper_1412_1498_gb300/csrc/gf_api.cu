@@ -122,7 +122,7 @@ int link_bytes(int storage) {
 
 struct Layout {
   size_t links, links64, staging, lats, lats64, tiles, unit_tiles, unit_lat, active, iters, partF,
-      pthe, ptho, part_blk, pending, usTo, unit_vol, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
+      pthe, ptho, pending, usTo, unit_vol, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
       unit_planes, ad_g, ad_delta, ad_part, ad_ticket, total;
   size_t staging_bytes;
   int max_tiles, n_units;
@@ -149,18 +149,15 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
     return at;
   };
   long long sites = 0, vmax = 0;
-  int max_tiles = 0, n_units = 0, unit_tiles_max = 0;
+  int max_tiles = 0, n_units = 0;
   for (int l = 0; l < n_lat; ++l) {
     const int* d = dims + 4 * l;
     long long V = (long long)d[0] * d[1] * d[2] * d[3];
     sites += V;
     vmax = std::max(vmax, V);
-    const int nt = tiles_for(d, kMinThreads);
-    max_tiles += nt;
+    max_tiles += tiles_for(d, kMinThreads);
     n_units += gauge == GF_LANDAU ? 1 : d[3];
-    unit_tiles_max = std::max(unit_tiles_max, gauge == GF_LANDAU ? nt : nt / d[3]);
   }
-  const int fin_blocks = (unit_tiles_max + kFinishThreads - 1) / kFinishThreads;
   L->links = take((size_t)sites * 4 * link_bytes(storage));
   const bool mixed = (flags & GF_FLAG_MIXED) && !is_fp64_storage(storage);
   L->links64 = mixed ? take((size_t)sites * 4 * 144) : (size_t)-1;
@@ -175,10 +172,9 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->unit_lat = take(sizeof(int) * n_units);
   L->active = take(sizeof(int) * n_units);
   L->iters = take(sizeof(int) * n_units);
-  L->partF = take(sizeof(double) * max_tiles);
-  L->pthe = take(sizeof(double) * max_tiles);
-  L->ptho = take(sizeof(double) * max_tiles);
-  L->part_blk = take(sizeof(double) * 3 * (size_t)n_units * fin_blocks);
+  L->partF = take(sizeof(float2) * max_tiles);
+  L->pthe = take(sizeof(float2) * max_tiles);
+  L->ptho = take(sizeof(float2) * max_tiles);
   L->pending = take(sizeof(int) * n_units);
   L->usTo = take(sizeof(double) * n_units);
   L->unit_vol = take(sizeof(double) * n_units);
@@ -240,7 +236,7 @@ int check_common(int n_lat, const int* dims, int gauge, int storage, int flags, 
       }
     }
     const size_t c = storage == GF_FP64_18 ? 16 : 8;
-    if (4 * (size_t)dims[0] * dims[1] * c > 200 * 1024) {
+    if (4 * (size_t)(dims[0] + 1) * dims[1] * c > 200 * 1024) {
       *why = "Lx * Ly too large for the shared-memory plane FFT";
       return GF_EINVAL;
     }
@@ -279,11 +275,10 @@ struct gf_handle {
   LatDev *d_lats = nullptr, *d_lats64 = nullptr;
   int4* d_tiles = nullptr;
   int *d_unit_tiles = nullptr, *d_unit_lat = nullptr, *d_active = nullptr, *d_iters = nullptr;
-  double *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr, *d_part_blk = nullptr,
-         *d_usTo = nullptr;
+  float2 *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr;  // per-tile pairs (hi, lo)
+  double* d_usTo = nullptr;
   int* d_pending = nullptr;
   double* d_unit_vol = nullptr;
-  int fin_blocks = 1;  // finishing blocks per unit for the current tile table
   double *d_usF = nullptr, *d_usT = nullptr, *d_uF = nullptr, *d_uT = nullptr, *d_lF = nullptr,
          *d_lT = nullptr;
   DevState* d_state = nullptr;
@@ -373,9 +368,6 @@ int build_tiles(gf_handle* h) {
   unit_tiles.push_back((int)tiles.size());
   if ((int)tiles.size() > h->L.max_tiles) return fail(h, GF_EINVAL, "tile table overflow");
   h->n_tiles = (int)tiles.size();
-  int most = 1;
-  for (size_t u = 0; u + 1 < unit_tiles.size(); ++u) most = std::max(most, unit_tiles[u + 1] - unit_tiles[u]);
-  h->fin_blocks = (most + kFinishThreads - 1) / kFinishThreads;
   GF_CK(h, cudaMemcpyAsync(h->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice, h->stream));
   GF_CK(h, cudaMemcpyAsync(h->d_unit_tiles, unit_tiles.data(), sizeof(int) * unit_tiles.size(),
                            cudaMemcpyHostToDevice, h->stream));
@@ -440,8 +432,6 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   a.part_F = h->d_partF;
   a.part_th_even = h->d_pthe;
   a.part_th_odd = h->d_ptho;
-  a.part_blk = h->d_part_blk;
-  a.blocks_per_unit = h->fin_blocks;
   a.pending = h->d_pending;
   a.unit_sumTh_odd = h->d_usTo;
   a.unit_sumF = h->d_usF;
@@ -723,10 +713,9 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   h->d_unit_lat = (int*)(w + L.unit_lat);
   h->d_active = (int*)(w + L.active);
   h->d_iters = (int*)(w + L.iters);
-  h->d_partF = (double*)(w + L.partF);
-  h->d_pthe = (double*)(w + L.pthe);
-  h->d_ptho = (double*)(w + L.ptho);
-  h->d_part_blk = (double*)(w + L.part_blk);
+  h->d_partF = (float2*)(w + L.partF);
+  h->d_pthe = (float2*)(w + L.pthe);
+  h->d_ptho = (float2*)(w + L.ptho);
   h->d_pending = (int*)(w + L.pending);
   h->d_usTo = (double*)(w + L.usTo);
   h->d_unit_vol = (double*)(w + L.unit_vol);

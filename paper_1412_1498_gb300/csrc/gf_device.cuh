@@ -552,4 +552,67 @@ __device__ __forceinline__ void block_sum_f32(const float (&v)[NV], double (&out
   }
 }
 
+// the same, leaving each total as the unevaluated pair (hi, lo) (valid in thread 0)
+template <int NV>
+__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float2 (&out)[NV],
+                                              float* smem /* 2 * NV * 32 */) {
+  float hi[NV], lo[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    hi[k] = v[k];
+    lo[k] = 0.f;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const float oh = __shfl_down_sync(0xffffffffu, hi[k], o);
+      const float ol = __shfl_down_sync(0xffffffffu, lo[k], o);
+      float s, e;
+      two_sum(hi[k], oh, s, e);
+      hi[k] = s;
+      lo[k] = (lo[k] + ol) + e;
+    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      smem[(2 * k) * 32 + warp] = hi[k];
+      smem[(2 * k + 1) * 32 + warp] = lo[k];
+    }
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float h = lane < nw ? smem[(2 * k) * 32 + lane] : 0.f;
+      float l = lane < nw ? smem[(2 * k + 1) * 32 + lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, h, o);
+        const float ol = __shfl_down_sync(0xffffffffu, l, o);
+        float s, e;
+        two_sum(h, oh, s, e);
+        h = s;
+        l = (l + ol) + e;
+      }
+      out[k] = make_float2(h, l);
+    }
+  }
+}
+
+// Unevaluated pairs hi + lo of floats ("double-float"): sums of per-tile partials are
+// formed with FP32 instructions only.  pair_of splits a double (48 of its 53 bits kept).
+__device__ __forceinline__ float2 pair_of(double d) {
+  const float hi = (float)d;
+  return make_float2(hi, (float)(d - (double)hi));
+}
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e += a.y + b.y;
+  const float hi = s + e;
+  return make_float2(hi, e - (hi - s));
+}
+__device__ __forceinline__ double pair_value(float2 a) { return (double)a.x + (double)a.y; }
+
 }  // namespace gf

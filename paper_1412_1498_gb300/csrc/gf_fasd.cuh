@@ -72,6 +72,67 @@ __device__ __forceinline__ void fft_lines(cx<T>* d, const cx<T>* tw, int n_lines
   }
 }
 
+// Lines of up to 32 points through registers: each thread transforms whole lines
+// (natural order in and out), no barrier between butterfly stages.  The transform is
+// decimation in frequency (Gentleman-Sande), which leaves the result in bit-reversed
+// order; the store undoes it with compile-time indices.  Same arguments and result as
+// fft_lines; lines longer than 32 points go to fft_lines.
+__host__ __device__ constexpr int bit_rev(int r, int logL) {
+  int o = 0;
+  for (int b = 0; b < logL; ++b) o |= ((r >> b) & 1) << (logL - 1 - b);
+  return o;
+}
+
+template <class T, int LOGL>
+__device__ __forceinline__ void fft_line_reg(cx<T>* d, int estride, const cx<T>* tw, int sign) {
+  constexpr int L = 1 << LOGL;
+  cx<T> v[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) v[k] = d[k * estride];
+#pragma unroll
+  for (int span = L / 2; span >= 1; span >>= 1) {
+#pragma unroll
+    for (int s = 0; s < L; s += 2 * span) {
+#pragma unroll
+      for (int j = 0; j < span; ++j) {
+        const cx<T> a = v[s + j], b = v[s + j + span];
+        v[s + j] = cadd(a, b);
+        cx<T> e = csub(a, b);
+        if (j != 0) {
+          cx<T> w = tw[j * (L / (2 * span))];  // exp(-2 pi i j / (2 span))
+          if (sign > 0) w.im = -w.im;
+          e = cmul(e, w);
+        }
+        v[s + j + span] = e;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < L; ++r) d[bit_rev(r, LOGL) * estride] = v[r];
+}
+
+template <class T>
+__device__ __forceinline__ void fft_lines_reg(cx<T>* d, const cx<T>* tw, int n_lines, int logL, int n_in,
+                                              int in_stride, int out_stride, int estride, int sign) {
+  if (logL > 5) {
+    fft_lines(d, tw, n_lines, logL, n_in, in_stride, out_stride, estride, sign);
+    return;
+  }
+  const int li = __ffs(n_in) - 1;
+  for (int l = threadIdx.x; l < n_lines; l += blockDim.x) {
+    cx<T>* p = d + (l & (n_in - 1)) * in_stride + (l >> li) * out_stride;
+    switch (logL) {
+      case 1: fft_line_reg<T, 1>(p, estride, tw, sign); break;
+      case 2: fft_line_reg<T, 2>(p, estride, tw, sign); break;
+      case 3: fft_line_reg<T, 3>(p, estride, tw, sign); break;
+      case 4: fft_line_reg<T, 4>(p, estride, tw, sign); break;
+      case 5: fft_line_reg<T, 5>(p, estride, tw, sign); break;
+      default: break;
+    }
+  }
+  __syncthreads();
+}
+
 template <class T>
 __device__ __forceinline__ void twiddles(cx<T>* tw, int logL) {
   const int L = 1 << logL;
@@ -133,7 +194,7 @@ __device__ __forceinline__ void g_load(const char* gbuf, long long V, int idx, c
 
 // ------------------------------------------------------------------------- A: Delta + FFT xy
 template <int S, int ND>
-__global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
+__global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_delta_xy(FasdArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   constexpr int NE = St::NE;
@@ -144,7 +205,8 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
   const LatDev& lat = a.lat;
   const int z = blockIdx.x, t = blockIdx.y;
   const int Lx = lat.L[0], Ly = lat.L[1], P = Lx * Ly;
-  cx<T>* pl = reinterpret_cast<cx<T>*>(smraw);  // [4][Ly][Lx]
+  const int pitch = Lx + 1;                      // padded rows: x-lines without bank conflicts
+  cx<T>* pl = reinterpret_cast<cx<T>*>(smraw);  // [4][Ly][pitch]
   twiddles(twx, a.logL[0]);
   twiddles(twy, a.logL[1]);
   T fsum = T(0), q = T(0);
@@ -183,10 +245,11 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) qq = qq + (D[e].re * D[e].re + D[e].im * D[e].im);
     q = q + qq;
-    pl[0 * P + i] = D[1];
-    pl[1 * P + i] = D[2];
-    pl[2 * P + i] = D[5];
-    pl[3 * P + i] = {D[0].im, D[4].im};
+    const int r = y * pitch + x, fs = Ly * pitch;
+    pl[r] = D[1];
+    pl[fs + r] = D[2];
+    pl[2 * fs + r] = D[5];
+    pl[3 * fs + r] = {D[0].im, D[4].im};
   }
   const T v[2] = {fsum, q};
   double o[2];
@@ -197,14 +260,14 @@ __global__ void __launch_bounds__(256) k_fasd_delta_xy(FasdArgs a) {
   }
   __syncthreads();
   // forward FFT along x (rows), then along y (columns), all four fields
-  fft_lines(pl, twx, 4 * Ly, a.logL[0], 1, 0, Lx, 1, -1);       // rows (f, y), along x
-  fft_lines(pl, twy, 4 * Lx, a.logL[1], Lx, 1, P, Lx, -1);       // columns (f, x), along y
+  fft_lines_reg(pl, twx, 4 * Ly, a.logL[0], 1, 0, pitch, 1, -1);            // rows (f, y), along x
+  fft_lines_reg(pl, twy, 4 * Lx, a.logL[1], Lx, 1, Ly * pitch, pitch, -1);  // columns (f, x), along y
   cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf);
   const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
 #pragma unroll 8
   for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
     const int f = i >> (a.logL[0] + a.logL[1]), j = i & (P - 1);
-    kb[f * lat.V + plane0 + j] = pl[i];
+    kb[f * lat.V + plane0 + j] = pl[(f * Ly + (j >> a.logL[0])) * pitch + (j & (Lx - 1))];
   }
 }
 
@@ -311,8 +374,8 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
     col[kxl + KX * z + pitch * tl] = kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl];
   }
   __syncthreads();
-  fft_lines(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);          // along z
-  if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, -1);  // along t
+  fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);          // along z
+  if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, -1);  // along t
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int kxl = i & mk, kz = (i >> lk) & mz, kt = i >> (lk + lz);
     T p2 = p2xy[kxl] + s2z[kz];
@@ -322,8 +385,8 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
     col[c] = cscale(col[c], fac);
   }
   __syncthreads();
-  if (ND == 4) fft_lines(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, +1);
-  fft_lines(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
+  if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, +1);
+  fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
 #pragma unroll 8
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);
@@ -333,7 +396,7 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
 
 // ------------------------------------------------------------------------- D: inverse xy, g
 template <int S, int ND>
-__global__ void __launch_bounds__(256) k_fasd_xy_inv_g(FasdArgs a) {
+__global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_xy_inv_g(FasdArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -343,23 +406,27 @@ __global__ void __launch_bounds__(256) k_fasd_xy_inv_g(FasdArgs a) {
   const int z = blockIdx.x, t = blockIdx.y;
   if (ND == 3 && a.active && !a.active[t]) return;
   const int Lx = lat.L[0], Ly = lat.L[1], P = Lx * Ly;
-  cx<T>* pl = reinterpret_cast<cx<T>*>(smraw);
+  const int pitch = Lx + 1;
+  cx<T>* pl = reinterpret_cast<cx<T>*>(smraw);  // [4][Ly][pitch]
   twiddles(twx, a.logL[0]);
   twiddles(twy, a.logL[1]);
   const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf);
   const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
 #pragma unroll 8
-  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x)
-    pl[i] = kb[(i >> (a.logL[0] + a.logL[1])) * lat.V + plane0 + (i & (P - 1))];
+  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+    const int f = i >> (a.logL[0] + a.logL[1]), j = i & (P - 1);
+    pl[(f * Ly + (j >> a.logL[0])) * pitch + (j & (Lx - 1))] = kb[f * lat.V + plane0 + j];
+  }
   __syncthreads();
-  fft_lines(pl, twy, 4 * Lx, a.logL[1], Lx, 1, P, Lx, +1);
-  fft_lines(pl, twx, 4 * Ly, a.logL[0], 1, 0, Lx, 1, +1);
+  fft_lines_reg(pl, twy, 4 * Lx, a.logL[1], Lx, 1, Ly * pitch, pitch, +1);
+  fft_lines_reg(pl, twx, 4 * Ly, a.logL[0], 1, 0, pitch, 1, +1);
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     const int x = i & (Lx - 1), y = i >> a.logL[0];
     const long long lexi = x + (long long)Lx * (y + (long long)Ly * (z + (long long)lat.L[2] * t));
     const int idx = ((x + y + z + t) & 1) * lat.Vh + (int)(lexi >> 1);
     // Delta~ (already scaled by alpha/2 p^2_max/p^2/N): anti-Hermitian, traceless
-    const cx<T> d01 = pl[i], d02 = pl[P + i], d12 = pl[2 * P + i], dd = pl[3 * P + i];
+    const int r = y * pitch + x, fs = Ly * pitch;
+    const cx<T> d01 = pl[r], d02 = pl[fs + r], d12 = pl[2 * fs + r], dd = pl[3 * fs + r];
     cx<T> g[9];
     g[0] = {T(1), dd.re};
     g[4] = {T(1), dd.im};

@@ -3,192 +3,203 @@
 
 namespace gf {
 
-// Two stages.  Block (u, j) adds tiles [j * kFinishThreads, (j + 1) * kFinishThreads) of
-// unit u with a fixed binary tree in shared memory (FP64 issues at ~1/64 of the FP32
-// rate here, so the tree does n - 1 additions instead of a shuffle tree's 5 n) and
-// stores the sums.  The last block to take a ticket adds each unit's block sums in
-// order and finishes the units, then the lattice totals and the loop state.  The order
-// of every addition is fixed: deterministic.
+// One block per unit adds the unit's tile partials, kept as pairs (hi, lo) of floats,
+// with FP32 instructions only (FP64 issues at ~1/64 of the FP32 rate here): each thread
+// sums a fixed stride of tiles, then a fixed binary tree in shared memory.  Thread 0
+// finishes the unit; the loop state is updated by the block itself when there is one
+// unit, else by the last block to take a ticket.  Every addition has a fixed order:
+// deterministic.
 //
 // Modes.  MEASURE / RESET (outside the loop): F and theta of every unit from the two
 // parity passes; RESET also sets the masks.  In the loop a check sweep runs ODD after
 // the odd half-sweep, which measured F and the odd-site part of theta: theta >= the
 // odd part (every Tr[Delta Delta^+] >= 0), so a unit whose odd part is already >= eps
 // continues, exactly as the full theta would decide; the others (and every unit on the
-// last sweep of the budget) are marked pending.  The even-site pass then runs for the
-// pending units only, and LOOP completes their theta and masks, counts the sweep and
-// updates the loop state.
+// last sweep of the budget) are pending.  With nothing pending ODD also does the
+// sweep's bookkeeping and closes it; otherwise the even-site pass runs for the pending
+// units and LOOP completes their theta and masks, counts the sweep and updates the
+// loop state.
 __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
-  __shared__ double red[3][kFinishThreads];
+  __shared__ float2 red[3][kFinishThreads];
   __shared__ int s_last;
   __shared__ int s_cnt[kFinishThreads / 32];
   const int tid = (int)threadIdx.x;
-  const int S = a.blocks_per_unit;
-  const int u = (int)blockIdx.x / S, j = (int)blockIdx.x - u * S;
+  const int u = (int)blockIdx.x;
   const bool loop = a.mode == FINISH_LOOP || a.mode == FINISH_ODD;
   bool check = true;
   if (loop) {
     if (!state_running(a.st)) return;  // uniform over the grid: nobody takes a ticket
     check = state_check_sweep(a.st);
     if (a.mode == FINISH_ODD && !check) {
-      if (blockIdx.x == 0 && tid == 0) a.st->sweep_closed = 0;
+      if (u == 0 && tid == 0) a.st->sweep_closed = 0;
       return;
     }
     if (a.mode == FINISH_LOOP && a.st->sweep_closed) return;  // written by the previous launch
   }
+  const bool was_active = a.active[u] != 0;
   bool reduce;
-  if (a.mode == FINISH_ODD) reduce = a.active[u] != 0;
-  else if (a.mode == FINISH_LOOP) reduce = check && a.active[u] != 0 && a.pending[u] != 0;
+  if (a.mode == FINISH_ODD) reduce = was_active;
+  else if (a.mode == FINISH_LOOP) reduce = check && was_active && a.pending[u] != 0;
   else reduce = true;
+  const double eps = a.st->eps;
+  // what thread 0 needs after the reduction, loaded while the tiles are summed
+  double vol = 0.0, uF_old = 0.0, uT_old = 0.0, uTo = 0.0;
+  int sweep = 0, limit = 0;
+  if (tid == 0) {
+    vol = a.unit_vol[u];
+    uF_old = a.unit_sumF[u];
+    uT_old = a.unit_sumTh[u];
+    uTo = a.unit_sumTh_odd[u];
+    sweep = a.st->sweep;
+    limit = a.st->limit;
+  }
   if (reduce) {
-    const int i = a.unit_tiles[u] + j * kFinishThreads + tid;
-    const bool in = i < a.unit_tiles[u + 1];
     const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET;
-    red[0][tid] = in && a.mode != FINISH_LOOP ? a.part_F[i] : 0.0;
-    red[1][tid] = in ? (a.mode == FINISH_ODD ? a.part_th_odd[i] : a.part_th_even[i]) : 0.0;
-    red[2][tid] = in && outside ? a.part_th_odd[i] : 0.0;
+    const float2* p1 = a.mode == FINISH_ODD ? a.part_th_odd : a.part_th_even;
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0;
+    const int te = a.unit_tiles[u + 1];
+    // kFinishUnroll tiles per thread and pass: all their loads are in flight together
+    for (int i0 = a.unit_tiles[u] + tid; i0 < te; i0 += kFinishUnroll * kFinishThreads) {
+      float2 x0[kFinishUnroll], x1[kFinishUnroll], x2[kFinishUnroll];
+#pragma unroll
+      for (int j = 0; j < kFinishUnroll; ++j) {
+        const int i = i0 + j * kFinishThreads;
+        const bool in = i < te;
+        x0[j] = in && a.mode != FINISH_LOOP ? a.part_F[i] : make_float2(0.f, 0.f);
+        x1[j] = in ? p1[i] : make_float2(0.f, 0.f);
+        x2[j] = in && outside ? a.part_th_odd[i] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < kFinishUnroll; ++j) {
+        acc0 = pair_add(acc0, x0[j]);
+        acc1 = pair_add(acc1, x1[j]);
+        acc2 = pair_add(acc2, x2[j]);
+      }
+    }
+    red[0][tid] = acc0;
+    red[1][tid] = acc1;
+    red[2][tid] = acc2;
     __syncthreads();
 #pragma unroll
     for (int w = kFinishThreads / 2; w > 0; w >>= 1) {
       if (tid < w) {
-        red[0][tid] += red[0][tid + w];
-        red[1][tid] += red[1][tid + w];
-        red[2][tid] += red[2][tid + w];
+        red[0][tid] = pair_add(red[0][tid], red[0][tid + w]);
+        red[1][tid] = pair_add(red[1][tid], red[1][tid + w]);
+        red[2][tid] = pair_add(red[2][tid], red[2][tid + w]);
       }
       __syncthreads();
     }
-    if (tid < 3) a.part_blk[3 * blockIdx.x + tid] = red[tid][0];
   }
-  __syncthreads();
   if (tid == 0) {
-    __threadfence();
-    const unsigned int t = atomicAdd(&a.st->ticket, 1u);
-    s_last = (t == gridDim.x - 1);
+    const bool forced = loop && sweep + 1 == limit;  // last sweep of the budget: measure exactly
+    const double s0 = reduce ? pair_value(red[0][0]) : 0.0;
+    const double s1 = reduce ? pair_value(red[1][0]) : 0.0;
+    const double s2 = reduce ? pair_value(red[2][0]) : 0.0;
+    double uF = uF_old, uT = uT_old;
+    int pend = 0;
+    bool act = was_active;
+    if (a.mode == FINISH_ODD) {
+      if (reduce) {
+        uF = s0;
+        a.unit_sumF[u] = s0;
+        a.unit_F[u] = s0 / ((double)a.nd * 3.0 * vol);
+        a.unit_sumTh_odd[u] = s1;
+        pend = forced || !(s1 / (3.0 * vol) >= eps);
+      }
+      a.pending[u] = pend;
+    } else {
+      if (reduce) {
+        uT = a.mode == FINISH_LOOP ? s1 + uTo : s1 + s2;
+        a.unit_sumTh[u] = uT;
+        a.unit_theta[u] = uT / (3.0 * vol);
+        if (a.mode != FINISH_LOOP) {
+          uF = s0;
+          a.unit_sumF[u] = s0;
+          a.unit_F[u] = s0 / ((double)a.nd * 3.0 * vol);
+        }
+        if (a.mode != FINISH_MEASURE) {
+          act = uT / (3.0 * vol) >= eps;
+          a.active[u] = act;
+        }
+      }
+      if (a.mode == FINISH_LOOP && was_active) a.iters[u] += 1;
+    }
+    if (a.n_units == 1) {
+      // one unit is one Landau lattice: the loop state follows from this thread's values
+      // (the same totals and counts as the general path below, without re-reading them)
+      if (a.mode == FINISH_ODD && pend) {
+        a.st->need_exact = 1;
+        a.st->sweep_closed = 0;
+      } else {
+        if (a.mode == FINISH_ODD && was_active) a.iters[u] += 1;
+        if (!loop || check) {
+          a.lat_F[0] = uF / ((double)a.nd * 3.0 * vol);
+          a.lat_theta[0] = uT / (3.0 * vol);
+        }
+        if (a.mode == FINISH_ODD) {
+          a.st->need_exact = 0;
+          a.st->sweep_closed = 1;
+        } else if (a.mode != FINISH_MEASURE) {
+          a.st->n_active = act ? 1 : 0;
+        }
+        if (loop) a.st->sweep = sweep + 1;
+      }
+      a.st->ticket = 0u;
+      s_last = 0;
+    } else {
+      __threadfence();
+      s_last = atomicAdd(&a.st->ticket, 1u) == (unsigned int)(a.n_units - 1);
+    }
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last block: every unit from its block sums, in order.  All loads of a unit are
-  // independent of one another; per-unit results stay in shared memory for the lattice
-  // totals when the units fit, so the tail is one round of loads, then stores.
-  __shared__ double s_uF[kFinishThreads], s_uT[kFinishThreads];
-  const bool small = a.n_units <= kFinishThreads;
-  int cnt = 0;  // ODD: pending units; otherwise: active units after this step
-  const double eps = a.st->eps;
-  const bool forced = loop && a.st->sweep + 1 == a.st->limit;  // last sweep: measure exactly
-  for (int v = tid; v < a.n_units; v += blockDim.x) {
-    const bool was_active = __ldcg(a.active + v) != 0;
-    const bool pend_in = a.mode == FINISH_LOOP && __ldcg(a.pending + v) != 0;
-    const double vol = a.unit_vol[v];
-    double uF = __ldcg(a.unit_sumF + v), uT = __ldcg(a.unit_sumTh + v);
-    const double uTo = a.mode == FINISH_LOOP ? __ldcg(a.unit_sumTh_odd + v) : 0.0;
-    bool red_v;
-    if (a.mode == FINISH_ODD) red_v = was_active;
-    else if (a.mode == FINISH_LOOP) red_v = check && was_active && pend_in;
-    else red_v = true;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-    if (red_v) {
-      const int nb = (a.unit_tiles[v + 1] - a.unit_tiles[v] + kFinishThreads - 1) / kFinishThreads;
-      for (int b = 0; b < nb; ++b) {
-        const double* p = a.part_blk + 3 * (v * S + b);
-        s0 += __ldcg(p);
-        s1 += __ldcg(p + 1);
-        s2 += __ldcg(p + 2);
-      }
-    }
-    bool act = was_active;
-    if (a.mode == FINISH_ODD) {
-      int pend = 0;
-      if (red_v) {
-        uF = s0;
-        a.unit_sumF[v] = s0;
-        a.unit_F[v] = s0 / ((double)a.nd * 3.0 * vol);
-        a.unit_sumTh_odd[v] = s1;
-        pend = forced || !(s1 / (3.0 * vol) >= eps);
-      }
-      a.pending[v] = pend;
-      cnt += pend;
-    } else {
-      if (red_v) {
-        uT = a.mode == FINISH_LOOP ? s1 + uTo : s1 + s2;
-        a.unit_sumTh[v] = uT;
-        a.unit_theta[v] = uT / (3.0 * vol);
-        if (a.mode != FINISH_LOOP) {
-          uF = s0;
-          a.unit_sumF[v] = s0;
-          a.unit_F[v] = s0 / ((double)a.nd * 3.0 * vol);
-        }
-        if (a.mode != FINISH_MEASURE) {
-          act = uT / (3.0 * vol) >= eps;
-          a.active[v] = act;
-        }
-      }
-      if (a.mode == FINISH_LOOP && was_active) a.iters[v] += 1;
-      cnt += act;
-    }
-    if (small) {
-      s_uF[v] = uF;
-      s_uT[v] = uT;
-    }
-  }
+  // the loop state: counts, lattice totals in a fixed order
+  int cnt = 0;  // ODD: pending units; otherwise: active units
+  for (int v = tid; v < a.n_units; v += blockDim.x)
+    cnt += a.mode == FINISH_ODD ? __ldcg(a.pending + v) : __ldcg(a.active + v);
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
   __syncthreads();
   int n = 0;
   for (int w = 0; w < kFinishThreads / 32; ++w) n += s_cnt[w];
-  if (a.mode == FINISH_ODD) {
-    if (n > 0) {
-      if (tid == 0) {
-        a.st->need_exact = 1;
-        a.st->sweep_closed = 0;
-        a.st->ticket = 0u;
-      }
-      return;
-    }
-    // nothing pending: every active unit continues, so the sweep's bookkeeping is done
-    // here and the even-site pass and FINISH_LOOP of this sweep do nothing
-    for (int v = tid; v < a.n_units; v += blockDim.x)
-      if (__ldcg(a.active + v) != 0) a.iters[v] += 1;
-    for (int l = tid; l < a.n_lat; l += blockDim.x) {
-      const LatDev lat = a.lats[l];
-      double sF = 0.0, sTh = 0.0;
-      for (int k = 0; k < lat.n_units; ++k) {
-        sF += small ? s_uF[lat.unit0 + k] : __ldcg(a.unit_sumF + lat.unit0 + k);
-        sTh += small ? s_uT[lat.unit0 + k] : __ldcg(a.unit_sumTh + lat.unit0 + k);
-      }
-      a.lat_F[l] = sF / ((double)a.nd * 3.0 * (double)lat.V);
-      a.lat_theta[l] = sTh / (3.0 * (double)lat.V);
-    }
+  if (a.mode == FINISH_ODD && n > 0) {
     if (tid == 0) {
-      a.st->need_exact = 0;
-      a.st->sweep_closed = 1;
-      a.st->sweep += 1;
+      a.st->need_exact = 1;
+      a.st->sweep_closed = 0;
       a.st->ticket = 0u;
     }
     return;
   }
-  // lattice totals in a fixed order, loop state
+  if (a.mode == FINISH_ODD)  // nothing pending: every active unit continues; close the sweep
+    for (int v = tid; v < a.n_units; v += blockDim.x)
+      if (__ldcg(a.active + v) != 0) a.iters[v] += 1;
   if (!loop || check) {
     for (int l = tid; l < a.n_lat; l += blockDim.x) {
       const LatDev lat = a.lats[l];
       double sF = 0.0, sTh = 0.0;
       for (int k = 0; k < lat.n_units; ++k) {
-        sF += small ? s_uF[lat.unit0 + k] : __ldcg(a.unit_sumF + lat.unit0 + k);
-        sTh += small ? s_uT[lat.unit0 + k] : __ldcg(a.unit_sumTh + lat.unit0 + k);
+        sF += __ldcg(a.unit_sumF + lat.unit0 + k);
+        sTh += __ldcg(a.unit_sumTh + lat.unit0 + k);
       }
       a.lat_F[l] = sF / ((double)a.nd * 3.0 * (double)lat.V);
       a.lat_theta[l] = sTh / (3.0 * (double)lat.V);
     }
   }
   if (tid == 0) {
-    if (a.mode != FINISH_MEASURE) a.st->n_active = n;
+    if (a.mode == FINISH_ODD) {
+      a.st->need_exact = 0;
+      a.st->sweep_closed = 1;
+    } else if (a.mode != FINISH_MEASURE) {
+      a.st->n_active = n;
+    }
     if (loop) a.st->sweep += 1;
     a.st->ticket = 0u;
   }
 }
 
 void launch_finish(const FinishArgs& a, cudaStream_t s) {
-  k_finish<<<a.n_units * a.blocks_per_unit, kFinishThreads, 0, s>>>(a);
+  k_finish<<<a.n_units, kFinishThreads, 0, s>>>(a);
 }
 
 // ---------------------------------------------------------------------------------

@@ -5,7 +5,7 @@ namespace gf {
 
 static size_t plane_smem(int storage, const LatDev& lat) {
   const size_t c = storage == GF_FP64_18 ? 16 : 8;
-  return 4 * (size_t)lat.L[0] * lat.L[1] * c;
+  return 4 * (size_t)(lat.L[0] + 1) * lat.L[1] * c;  // rows padded by one element
 }
 static size_t column_smem(int storage, int nd, const LatDev& lat) {
   const size_t c = storage == GF_FP64_18 ? 16 : 8;

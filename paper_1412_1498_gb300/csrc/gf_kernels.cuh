@@ -178,6 +178,21 @@ __device__ __forceinline__ void tile_sum(const T (&v)[NV], double (&out)[NV], do
   }
 }
 
+// the same with each total as a pair (hi, lo) for the finishing reduction
+template <class T, int NV>
+__device__ __forceinline__ void tile_sum(const T (&v)[NV], float2 (&out)[NV], double* smem64) {
+  if constexpr (sizeof(T) == 8) {
+    double w[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) w[k] = v[k];
+    block_sum<NV>(w, smem64);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) out[k] = pair_of(w[k]);
+  } else {
+    block_sum_f32<NV>(v, out, reinterpret_cast<float*>(smem64));
+  }
+}
+
 // ----------------------------------------------------------------------------------
 // Kernel arguments
 // ----------------------------------------------------------------------------------
@@ -187,8 +202,8 @@ struct SweepArgs {
   const int4* tiles;       // (lat, t, first h3, unit) per block
   const int* active;       // per unit (nullable: all active)
   const DevState* st;      // nullable; when set, the loop state decides everything
-  double* part_theta;      // per tile: theta partial of the updated (odd) sites
-  double* part_F;          // nullable; per tile: Re Tr of the updated sites' 2 nd links
+  float2* part_theta;      // per tile: theta partial of the updated (odd) sites (hi, lo)
+  float2* part_F;          // nullable; per tile: Re Tr of the updated sites' 2 nd links
   int parity;
   int form;
   int reunit;              // used when st == nullptr
@@ -204,29 +219,28 @@ struct MeasureArgs {
   const int4* tiles;
   const int* active;       // nullable
   const DevState* st;      // nullable; when set, only runs on check sweeps
-  double* part_F;          // nullable: per tile sum of Re Tr over the 2 nd links of each site
-  double* part_theta;      // per tile sum of Tr[Delta Delta^+]
+  float2* part_F;          // nullable: per tile sum of Re Tr over the 2 nd links of each site
+  float2* part_theta;      // per tile sum of Tr[Delta Delta^+] (pairs hi, lo)
   int parity;
   int n_tiles;
   int reverse;
 };
 
-constexpr int kFinishThreads = 256;  // tiles summed by one block of the finishing kernel
+constexpr int kFinishThreads = 256;  // threads of a finishing block (one block per unit)
+constexpr int kFinishUnroll = 16;    // tile partials a finishing thread loads at once
 
 struct FinishArgs {
   const LatDev* lats;
   const int* unit_tiles;   // n_units + 1 tile boundaries
-  double* part_blk;        // 3 sums per finishing block
-  int blocks_per_unit;     // finishing blocks per unit: ceil(max tiles of a unit / kFinishThreads)
   int* pending;            // per unit: this check needs the even-site pass (FINISH_ODD sets it)
   double* unit_sumTh_odd;  // per unit: odd-site part of the theta sum of the current check
   const int* unit_lat;     // lattice of each unit
   const double* unit_vol;  // sites of each unit (Landau: V, Coulomb: Lx Ly Lz)
   int* active;
   int* iters;
-  const double* part_F;
-  const double* part_th_even;
-  const double* part_th_odd;
+  const float2* part_F;    // per-tile partials as pairs (hi, lo)
+  const float2* part_th_even;
+  const float2* part_th_odd;
   double* unit_sumF;
   double* unit_sumTh;
   double* unit_F;
@@ -383,7 +397,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   }
   if (measure_now) {
     const T v[2] = {fs, q};
-    double o[2];
+    float2 o[2];
     tile_sum<T, 2>(v, o, red);
     if (threadIdx.x == 0) {
       if (a.part_F) a.part_F[ti] = o[0];
@@ -445,7 +459,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
     q = theta_site(A);
   }
   const T v[2] = {fsum, q};
-  double o[2];
+  float2 o[2];
   tile_sum<T, 2>(v, o, red);
   if (threadIdx.x == 0) {
     if (a.part_F) a.part_F[ti] = o[0];

@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
   }
   if (measure_now) {
     const float v[2] = {fsum, q};
-    double o[2];
+    float2 o[2];
     block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
     if (threadIdx.x == 0) {
       if (a.part_F) a.part_F[ti] = o[0];
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(128) k_measure_split(MeasureArgs a) {
     q = split_theta_site(A);
   }
   const float v[2] = {fsum, q};
-  double o[2];
+  float2 o[2];
   block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
   if (threadIdx.x == 0) {
     if (a.part_F) a.part_F[ti] = o[0];

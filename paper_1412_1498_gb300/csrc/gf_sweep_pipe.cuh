@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
       }
       if (measure_now) {
         const float v[2] = {fs, q};
-        double o[2];
+        float2 o[2];
         block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
         if (threadIdx.x == 0) {
           if (a.part_F) a.part_F[cur.ti] = o[0];
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
         q = theta_site(A);
       }
       const float v[2] = {fsum, q};
-      double o[2];
+      float2 o[2];
       block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
       if (threadIdx.x == 0) {
         if (a.part_F) a.part_F[cur.ti] = o[0];
