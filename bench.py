@@ -443,7 +443,8 @@ def main():
     ap.add_argument("--skip-time-to-theta", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--split-probe", type=int, default=100)
-    ap.add_argument("--fasd-iters", type=int, default=50)
+    # 63 iterations and the final measurement fill four 16-iteration graph replays exactly
+    ap.add_argument("--fasd-iters", type=int, default=63)
     ap.add_argument("--autograd", type=int, default=1)
     ap.add_argument("--launch", default="", help="fixed launch shape THREADS:register|pipelined "
                     "instead of the autotuner (for profiler runs)")

@@ -122,7 +122,7 @@ int link_bytes(int storage) {
 
 struct Layout {
   size_t links, links64, staging, lats, lats64, tiles, unit_tiles, unit_lat, active, iters, partF,
-      pthe, ptho, pending, usTo, unit_vol, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
+      pthe, ptho, pending, usTo, unit_norm, usF, usT, uF, uT, lF, lT, state, kbuf, gbuf, planeF, planeT,
       unit_planes, ad_g, ad_delta, ad_part, ad_ticket, total;
   size_t staging_bytes;
   int max_tiles, n_units;
@@ -177,7 +177,7 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->ptho = take(sizeof(float2) * max_tiles);
   L->pending = take(sizeof(int) * n_units);
   L->usTo = take(sizeof(double) * n_units);
-  L->unit_vol = take(sizeof(double) * n_units);
+  L->unit_norm = take(sizeof(double) * 2 * n_units);
   L->usF = take(sizeof(double) * n_units);
   L->usT = take(sizeof(double) * n_units);
   L->uF = take(sizeof(double) * n_units);
@@ -191,8 +191,8 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
     const long long V = (long long)d[0] * d[1] * d[2] * d[3];
     L->kbuf = take(4 * (size_t)V * c);
     L->gbuf = take(6 * (size_t)V * c);
-    L->planeF = take(sizeof(double) * d[2] * d[3]);
-    L->planeT = take(sizeof(double) * d[2] * d[3]);
+    L->planeF = take(sizeof(float2) * d[2] * d[3]);
+    L->planeT = take(sizeof(float2) * d[2] * d[3]);
     L->unit_planes = take(sizeof(int) * (n_units + 1));
   } else {
     L->kbuf = L->gbuf = L->planeF = L->planeT = L->unit_planes = (size_t)-1;
@@ -278,7 +278,7 @@ struct gf_handle {
   float2 *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr;  // per-tile pairs (hi, lo)
   double* d_usTo = nullptr;
   int* d_pending = nullptr;
-  double* d_unit_vol = nullptr;
+  double* d_unit_norm = nullptr;
   double *d_usF = nullptr, *d_usT = nullptr, *d_uF = nullptr, *d_uT = nullptr, *d_lF = nullptr,
          *d_lT = nullptr;
   DevState* d_state = nullptr;
@@ -294,7 +294,7 @@ struct gf_handle {
   double alpha = 0.08;
   void* kbuf = nullptr;
   char* gbuf = nullptr;
-  double *d_planeF = nullptr, *d_planeT = nullptr;
+  float2 *d_planeF = nullptr, *d_planeT = nullptr;
   int* d_unit_planes = nullptr;
   void *ad_g = nullptr, *ad_delta = nullptr;
   double* ad_part = nullptr;
@@ -373,12 +373,14 @@ int build_tiles(gf_handle* h) {
                            cudaMemcpyHostToDevice, h->stream));
   GF_CK(h, cudaMemcpyAsync(h->d_unit_lat, unit_lat.data(), sizeof(int) * unit_lat.size(),
                            cudaMemcpyHostToDevice, h->stream));
-  std::vector<double> unit_vol;
+  std::vector<double> unit_norm;
   for (int l : unit_lat) {
     const LatDev& lat = h->lats[l];
-    unit_vol.push_back(h->gauge == GF_LANDAU ? (double)lat.V : 2.0 * lat.V3h);
+    const double vol = h->gauge == GF_LANDAU ? (double)lat.V : 2.0 * lat.V3h;
+    unit_norm.push_back(1.0 / ((double)h->nd * 3.0 * vol));
+    unit_norm.push_back(1.0 / (3.0 * vol));
   }
-  GF_CK(h, cudaMemcpyAsync(h->d_unit_vol, unit_vol.data(), sizeof(double) * unit_vol.size(),
+  GF_CK(h, cudaMemcpyAsync(h->d_unit_norm, unit_norm.data(), sizeof(double) * unit_norm.size(),
                            cudaMemcpyHostToDevice, h->stream));
   GF_CK(h, cudaStreamSynchronize(h->stream));  // host vectors die on return
   drop_graphs(h);
@@ -425,8 +427,9 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   FinishArgs a{};
   a.lats = cur_lats(h);
   a.unit_tiles = h->d_unit_tiles;
+  a.n_tiles = h->n_tiles;
   a.unit_lat = h->d_unit_lat;
-  a.unit_vol = h->d_unit_vol;
+  a.unit_norm = h->d_unit_norm;
   a.active = h->d_active;
   a.iters = h->d_iters;
   a.part_F = h->d_partF;
@@ -575,6 +578,7 @@ FasdArgs fasd_args(gf_handle* h, bool loop, int mode) {
   }
   const double nfft = h->nd == 4 ? (double)a.lat.V : 2.0 * a.lat.V3h;
   a.coef = 0.5 * h->alpha * (4.0 * h->nd) / nfft;
+  a.kx = fasd_kx(a.lat, h->nd, h->storage == GF_FP64_18 ? 16 : 8);
   return a;
 }
 
@@ -718,7 +722,7 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   h->d_ptho = (float2*)(w + L.ptho);
   h->d_pending = (int*)(w + L.pending);
   h->d_usTo = (double*)(w + L.usTo);
-  h->d_unit_vol = (double*)(w + L.unit_vol);
+  h->d_unit_norm = (double*)(w + L.unit_norm);
   if (cudaMemsetAsync(h->d_pending, 0, sizeof(int) * L.n_units, h->stream) != cudaSuccess)
     return bail(GF_ECUDA, "initialisation of the pending masks failed");
   h->d_usF = (double*)(w + L.usF);
@@ -740,8 +744,8 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   if (h->flags & GF_FLAG_FASD) {
     h->kbuf = w + L.kbuf;
     h->gbuf = w + L.gbuf;
-    h->d_planeF = (double*)(w + L.planeF);
-    h->d_planeT = (double*)(w + L.planeT);
+    h->d_planeF = (float2*)(w + L.planeF);
+    h->d_planeT = (float2*)(w + L.planeT);
     h->d_unit_planes = (int*)(w + L.unit_planes);
   }
 

@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_delta_xy(
     pl[3 * fs + r] = {D[0].im, D[4].im};
   }
   const T v[2] = {fsum, q};
-  double o[2];
+  float2 o[2];
   tile_sum<T, 2>(v, o, red);
   if (threadIdx.x == 0) {
     a.plane_F[z + lat.L[2] * t] = o[0];
@@ -272,38 +272,90 @@ __global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_delta_xy(
 }
 
 // ------------------------------------------------------------------------- B: finish
+// As the overrelaxation loop's finishing kernel: one block per unit adds the unit's
+// plane partials (float pairs, FP32 instructions only, fixed order); one unit updates
+// the loop state directly, several through a ticket.
 __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
-  __shared__ double red[96];
+  __shared__ float2 red[2][256];
   __shared__ int s_last;
-  if (a.st && a.mode == FINISH_LOOP && (a.st->n_active <= 0 || a.st->stop)) return;
-  const int u = blockIdx.x;
+  __shared__ int s_cnt[8];
+  const int tid = (int)threadIdx.x, u = (int)blockIdx.x;
+  const bool loop = a.st && a.mode == FINISH_LOOP;
+  int n_active = 1, stop = 0, sweep = 0, limit = 0;
+  double eps = 0.0;
+  if (a.st) {
+    n_active = a.st->n_active;
+    stop = a.st->stop;
+    sweep = a.st->sweep;
+    limit = a.st->limit;
+    eps = a.st->eps;
+  }
   const bool was_active = a.active == nullptr || a.active[u] != 0;
-  if (a.mode != FINISH_LOOP || was_active) {
-    const int pb = a.unit_planes[u], pe = a.unit_planes[u + 1];
-    double v[2] = {0.0, 0.0};
-    for (int i = pb + (int)threadIdx.x; i < pe; i += blockDim.x) {
-      v[0] += a.plane_F[i];
-      v[1] += a.plane_th[i];
+  const int pb = a.unit_planes[u], pe = a.unit_planes[u + 1];
+  if (loop && (n_active <= 0 || stop)) return;
+  const bool reduce = a.mode != FINISH_LOOP || was_active;
+  if (reduce) {
+    float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0;
+    for (int i0 = pb + tid; i0 < pe; i0 += 4 * 256) {
+      float2 x0[4], x1[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int i = i0 + j * 256;
+        x0[j] = i < pe ? a.plane_F[i] : make_float2(0.f, 0.f);
+        x1[j] = i < pe ? a.plane_th[i] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        acc0 = pair_add(acc0, x0[j]);
+        acc1 = pair_add(acc1, x1[j]);
+      }
     }
-    double w[3] = {v[0], v[1], 0.0};
-    block_sum<3>(w, red);
-    if (threadIdx.x == 0) {
-      const double vol = a.nd == 4 ? (double)a.lat.V : 2.0 * a.lat.V3h;
-      a.unit_sumF[u] = w[0];
-      a.unit_sumTh[u] = w[1];
-      a.unit_F[u] = w[0] / ((double)a.nd * 3.0 * vol);
-      a.unit_theta[u] = w[1] / (3.0 * vol);
-      if (a.mode == FINISH_LOOP && a.active) a.active[u] = a.unit_theta[u] >= a.st->eps;
+    red[0][tid] = acc0;
+    red[1][tid] = acc1;
+    __syncthreads();
+#pragma unroll
+    for (int w = 128; w > 0; w >>= 1) {
+      if (tid < w) {
+        red[0][tid] = pair_add(red[0][tid], red[0][tid + w]);
+        red[1][tid] = pair_add(red[1][tid], red[1][tid + w]);
+      }
+      __syncthreads();
     }
   }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    s_last = atomicAdd(&a.st->ticket, 1u) == (unsigned int)(a.n_units - 1);
+  if (tid == 0) {
+    const double vol = a.nd == 4 ? (double)a.lat.V : 2.0 * a.lat.V3h;
+    bool act = was_active;
+    if (reduce) {
+      const double sF = pair_value(red[0][0]), sT = pair_value(red[1][0]);
+      a.unit_sumF[u] = sF;
+      a.unit_sumTh[u] = sT;
+      a.unit_F[u] = sF / ((double)a.nd * 3.0 * vol);
+      a.unit_theta[u] = sT / (3.0 * vol);
+      if (loop && a.active) {
+        act = sT / (3.0 * vol) >= eps;
+        a.active[u] = act;
+      }
+      if (a.n_units == 1) {
+        a.lat_F[0] = sF / ((double)a.nd * 3.0 * (double)a.lat.V);
+        a.lat_theta[0] = sT / (3.0 * (double)a.lat.V);
+      }
+    }
+    if (a.n_units == 1 || a.st == nullptr) {
+      if (loop && a.active) {
+        a.st->n_active = act ? 1 : 0;
+        if (sweep >= limit) a.st->stop = 1;  // the field after the last allowed update is measured
+      }
+      if (a.st) a.st->ticket = 0u;
+      s_last = 0;
+    } else {
+      __threadfence();
+      s_last = atomicAdd(&a.st->ticket, 1u) == (unsigned int)(a.n_units - 1);
+    }
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double sF = 0.0, sT = 0.0;
     for (int k = 0; k < a.n_units; ++k) {
       sF += __ldcg(a.unit_sumF + k);
@@ -312,22 +364,26 @@ __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
     a.lat_F[0] = sF / ((double)a.nd * 3.0 * (double)a.lat.V);
     a.lat_theta[0] = sT / (3.0 * (double)a.lat.V);
   }
-  double c[1] = {0.0};
+  int c = 0;
   if (a.active)
-    for (int k = threadIdx.x; k < a.n_units; k += blockDim.x) c[0] += (double)__ldcg(a.active + k);
-  block_sum<1>(c, red);
-  if (threadIdx.x == 0) {
-    if (a.mode == FINISH_LOOP && a.active) {
-      a.st->n_active = (int)c[0];
-      // the field after the last allowed update has now been measured
-      if (a.st->sweep >= a.st->limit) a.st->stop = 1;
+    for (int k = tid; k < a.n_units; k += blockDim.x) c += __ldcg(a.active + k);
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((tid & 31) == 0) s_cnt[tid >> 5] = c;
+  __syncthreads();
+  if (tid == 0) {
+    int n = 0;
+    for (int w = 0; w < 8; ++w) n += s_cnt[w];
+    if (loop && a.active) {
+      a.st->n_active = n;
+      if (sweep >= limit) a.st->stop = 1;  // the field after the last allowed update is measured
     }
     a.st->ticket = 0u;
   }
 }
 
 // ------------------------------------------------------------------------- C: FFT z(t), filter
-// Block: one field, one ky, KX consecutive kx and (Coulomb) one t.  Shared layout
+// Block: one field, one ky, KX consecutive kx (KX = a.kx <= 8, chosen on the host so the
+// block fits in shared memory) and (Coulomb) one t.  Shared layout
 // col[kxl + KX z + (KX Lz + 4) tl]: the pad keeps both transform directions free of bank
 // conflicts.
 template <class T, int ND>
@@ -339,7 +395,7 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
   const LatDev& lat = a.lat;
   const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2], Lt = lat.L[3];
   const int lz = a.logL[2];
-  const int KX = Lx < 4 ? Lx : 4, lk = KX == 4 ? 2 : (KX == 2 ? 1 : 0);
+  const int KX = a.kx, lk = __ffs(KX) - 1;
   const int kx0 = blockIdx.x * KX, ky = blockIdx.y;
   const int f = ND == 4 ? (int)blockIdx.z : (int)blockIdx.z & 3;
   const int t0 = ND == 4 ? 0 : (int)blockIdx.z >> 2, nt = ND == 4 ? Lt : 1;
@@ -357,9 +413,9 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
       const T sn = sinpi((T)k / (T)Lt);
       s2t[k] = T(4) * sn * sn;
     }
-  T p2xy[4];
+  T p2xy[8];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
+  for (int j = 0; j < 8; ++j) {
     const T sx = sinpi((T)(kx0 + (j < KX ? j : 0)) / (T)Lx), sy = sinpi((T)ky / (T)Ly);
     p2xy[j] = T(4) * sx * sx + T(4) * sy * sy;
   }
@@ -446,37 +502,39 @@ __global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
   constexpr int NE = St::NE;
   if (!fasd_running(a.st)) return;
   const LatDev& lat = a.lat;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= lat.V) return;
-  const int p = i >= lat.Vh ? 1 : 0;
-  const int h = (int)(i - (long long)p * lat.Vh);
-  const Site s = site_of(lat, p, h);
-  // Coulomb gauge with per-slice masks: g = 1 on the sites of a converged slice, so its
-  // spatial links stay as they are while a temporal link into an active slice still
-  // takes that slice's g(x + t)^+ on the right
-  bool act = true, act_next = true;
-  if (ND == 3 && a.active) {
-    act = a.active[s.t] != 0;
-    act_next = a.active[s.t == lat.L[3] - 1 ? 0 : s.t + 1] != 0;
-    if (!act && !act_next) return;
-  }
   const bool reunit_now = a.st ? state_reunit_sweep(a.st) : a.reunit != 0;
   char* base = a.links + lat.off_bytes;
-  cx<T> g[9];
-  if (act) g_load<T>(a.gbuf, lat.V, (int)i, g);
-#pragma unroll 1
-  for (int mu = 0; mu < 4; ++mu) {
-    const bool act_fwd = mu == 3 ? act_next : act;
-    if (!act && !act_fwd) continue;
-    cx<T> u[NE], gn[9];
-    St::load(base, lat.V, mu, (int)i, u);
-    if (act) left_mul(g, u);
-    if (act_fwd) {
-      g_load<T>(a.gbuf, lat.V, (1 - p) * lat.Vh + (int)(fwd_lexi(lat, s, mu) >> 1), gn);
-      right_mul_dag(u, gn);
+  // grid-stride over the sites (a small persistent grid: cheap when the loop is over)
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < lat.V;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int p = i >= lat.Vh ? 1 : 0;
+    const int h = (int)(i - (long long)p * lat.Vh);
+    const Site s = site_of(lat, p, h);
+    // Coulomb gauge with per-slice masks: g = 1 on the sites of a converged slice, so its
+    // spatial links stay as they are while a temporal link into an active slice still
+    // takes that slice's g(x + t)^+ on the right
+    bool act = true, act_next = true;
+    if (ND == 3 && a.active) {
+      act = a.active[s.t] != 0;
+      act_next = a.active[s.t == lat.L[3] - 1 ? 0 : s.t + 1] != 0;
+      if (!act && !act_next) continue;
     }
-    if (reunit_now) reunit(u);
-    St::store(base, lat.V, mu, (int)i, u);
+    cx<T> g[9];
+    if (act) g_load<T>(a.gbuf, lat.V, (int)i, g);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      const bool act_fwd = mu == 3 ? act_next : act;
+      if (!act && !act_fwd) continue;
+      cx<T> u[NE], gn[9];
+      St::load(base, lat.V, mu, (int)i, u);
+      if (act) left_mul(g, u);
+      if (act_fwd) {
+        g_load<T>(a.gbuf, lat.V, (1 - p) * lat.Vh + (int)(fwd_lexi(lat, s, mu) >> 1), gn);
+        right_mul_dag(u, gn);
+      }
+      if (reunit_now) reunit(u);
+      St::store(base, lat.V, mu, (int)i, u);
+    }
   }
 }
 

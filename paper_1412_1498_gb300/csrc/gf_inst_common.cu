@@ -26,40 +26,44 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   const int tid = (int)threadIdx.x;
   const int u = (int)blockIdx.x;
   const bool loop = a.mode == FINISH_LOOP || a.mode == FINISH_ODD;
+  // Every load that does not depend on another one is issued here, together: the
+  // kernel is short and its time is mostly dependent round trips to memory.
+  const int n_active = a.st->n_active, sweep = a.st->sweep, limit = a.st->limit;
+  const int ci = a.st->check_interval, closed = a.st->sweep_closed;
+  const double eps = a.st->eps;
+  const bool was_active = a.active[u] != 0;
+  const bool pend_in = a.pending[u] != 0;
+  const int tb = a.n_units == 1 ? 0 : a.unit_tiles[u];
+  const int te = a.n_units == 1 ? a.n_tiles : a.unit_tiles[u + 1];
+  // what thread 0 needs after the reduction
+  double invF = 0.0, invT = 0.0, uF_old = 0.0, uT_old = 0.0, uTo = 0.0;
+  if (tid == 0) {
+    invF = a.unit_norm[2 * u];
+    invT = a.unit_norm[2 * u + 1];
+    uF_old = a.unit_sumF[u];
+    uT_old = a.unit_sumTh[u];
+    uTo = a.unit_sumTh_odd[u];
+  }
   bool check = true;
   if (loop) {
-    if (!state_running(a.st)) return;  // uniform over the grid: nobody takes a ticket
-    check = state_check_sweep(a.st);
+    if (!(n_active > 0 && sweep < limit)) return;  // uniform over the grid: no ticket taken
+    check = ((sweep + 1) % ci) == 0 || sweep + 1 == limit;  // state_check_sweep
     if (a.mode == FINISH_ODD && !check) {
       if (u == 0 && tid == 0) a.st->sweep_closed = 0;
       return;
     }
-    if (a.mode == FINISH_LOOP && a.st->sweep_closed) return;  // written by the previous launch
+    if (a.mode == FINISH_LOOP && closed) return;  // written by the previous launch
   }
-  const bool was_active = a.active[u] != 0;
   bool reduce;
   if (a.mode == FINISH_ODD) reduce = was_active;
-  else if (a.mode == FINISH_LOOP) reduce = check && was_active && a.pending[u] != 0;
+  else if (a.mode == FINISH_LOOP) reduce = check && was_active && pend_in;
   else reduce = true;
-  const double eps = a.st->eps;
-  // what thread 0 needs after the reduction, loaded while the tiles are summed
-  double vol = 0.0, uF_old = 0.0, uT_old = 0.0, uTo = 0.0;
-  int sweep = 0, limit = 0;
-  if (tid == 0) {
-    vol = a.unit_vol[u];
-    uF_old = a.unit_sumF[u];
-    uT_old = a.unit_sumTh[u];
-    uTo = a.unit_sumTh_odd[u];
-    sweep = a.st->sweep;
-    limit = a.st->limit;
-  }
   if (reduce) {
     const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET;
     const float2* p1 = a.mode == FINISH_ODD ? a.part_th_odd : a.part_th_even;
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0;
-    const int te = a.unit_tiles[u + 1];
     // kFinishUnroll tiles per thread and pass: all their loads are in flight together
-    for (int i0 = a.unit_tiles[u] + tid; i0 < te; i0 += kFinishUnroll * kFinishThreads) {
+    for (int i0 = tb + tid; i0 < te; i0 += kFinishUnroll * kFinishThreads) {
       float2 x0[kFinishUnroll], x1[kFinishUnroll], x2[kFinishUnroll];
 #pragma unroll
       for (int j = 0; j < kFinishUnroll; ++j) {
@@ -102,23 +106,23 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
       if (reduce) {
         uF = s0;
         a.unit_sumF[u] = s0;
-        a.unit_F[u] = s0 / ((double)a.nd * 3.0 * vol);
+        a.unit_F[u] = s0 * invF;
         a.unit_sumTh_odd[u] = s1;
-        pend = forced || !(s1 / (3.0 * vol) >= eps);
+        pend = forced || !(s1 * invT >= eps);
       }
       a.pending[u] = pend;
     } else {
       if (reduce) {
         uT = a.mode == FINISH_LOOP ? s1 + uTo : s1 + s2;
         a.unit_sumTh[u] = uT;
-        a.unit_theta[u] = uT / (3.0 * vol);
+        a.unit_theta[u] = uT * invT;
         if (a.mode != FINISH_LOOP) {
           uF = s0;
           a.unit_sumF[u] = s0;
-          a.unit_F[u] = s0 / ((double)a.nd * 3.0 * vol);
+          a.unit_F[u] = s0 * invF;
         }
         if (a.mode != FINISH_MEASURE) {
-          act = uT / (3.0 * vol) >= eps;
+          act = uT * invT >= eps;
           a.active[u] = act;
         }
       }
@@ -133,8 +137,8 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
       } else {
         if (a.mode == FINISH_ODD && was_active) a.iters[u] += 1;
         if (!loop || check) {
-          a.lat_F[0] = uF / ((double)a.nd * 3.0 * vol);
-          a.lat_theta[0] = uT / (3.0 * vol);
+          a.lat_F[0] = uF * invF;
+          a.lat_theta[0] = uT * invT;
         }
         if (a.mode == FINISH_ODD) {
           a.st->need_exact = 0;
@@ -182,8 +186,9 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
         sF += __ldcg(a.unit_sumF + lat.unit0 + k);
         sTh += __ldcg(a.unit_sumTh + lat.unit0 + k);
       }
-      a.lat_F[l] = sF / ((double)a.nd * 3.0 * (double)lat.V);
-      a.lat_theta[l] = sTh / (3.0 * (double)lat.V);
+      // the reciprocals as the host forms the per-unit ones (same bits for one-unit lattices)
+      a.lat_F[l] = sF * (1.0 / ((double)a.nd * 3.0 * (double)lat.V));
+      a.lat_theta[l] = sTh * (1.0 / (3.0 * (double)lat.V));
     }
   }
   if (tid == 0) {

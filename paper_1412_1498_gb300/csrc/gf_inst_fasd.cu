@@ -9,7 +9,7 @@ static size_t plane_smem(int storage, const LatDev& lat) {
 }
 static size_t column_smem(int storage, int nd, const LatDev& lat) {
   const size_t c = storage == GF_FP64_18 ? 16 : 8;
-  const int KX = lat.L[0] < 4 ? lat.L[0] : 4;
+  const int KX = fasd_kx(lat, nd, c);
   return (size_t)(nd == 4 ? lat.L[3] : 1) * (lat.L[2] * KX + 4) * c;
 }
 
@@ -47,8 +47,7 @@ void launch_fasd_delta_xy(int storage, int nd, const FasdArgs& a, cudaStream_t s
 void launch_fasd_finish(const FasdArgs& a, cudaStream_t s) { k_fasd_finish<<<a.n_units, 256, 0, s>>>(a); }
 
 void launch_fasd_zt(int storage, int nd, const FasdArgs& a, cudaStream_t s) {
-  const int KX = a.lat.L[0] < 4 ? a.lat.L[0] : 4;
-  const dim3 grid(a.lat.L[0] / KX, a.lat.L[1], nd == 4 ? 4 : 4 * a.lat.L[3]);
+  const dim3 grid(a.lat.L[0] / a.kx, a.lat.L[1], nd == 4 ? 4 : 4 * a.lat.L[3]);
   const size_t sm = column_smem(storage, nd, a.lat);
 #define GF_CALL(S, T, ND) k_fasd_zt<T, ND><<<grid, 256, sm, s>>>(a)
   GF_FASD_SWITCH(storage, nd, GF_CALL)
@@ -64,7 +63,12 @@ void launch_fasd_xy_inv_g(int storage, int nd, const FasdArgs& a, cudaStream_t s
 }
 
 void launch_fasd_update(int storage, int nd, const FasdArgs& a, cudaStream_t s) {
-  const unsigned int nb = (unsigned int)((a.lat.V + 127) / 128);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  const long long want = (a.lat.V + 127) / 128, cap = 8LL * sms;  // 8 blocks of 128 per SM
+  const unsigned int nb = (unsigned int)(want < cap ? want : cap);
 #define GF_CALL(S, T, ND) k_fasd_update<S, ND><<<nb, 128, 0, s>>>(a)
   GF_FASD_SWITCH(storage, nd, GF_CALL)
 #undef GF_CALL

@@ -232,10 +232,11 @@ constexpr int kFinishUnroll = 16;    // tile partials a finishing thread loads a
 struct FinishArgs {
   const LatDev* lats;
   const int* unit_tiles;   // n_units + 1 tile boundaries
+  int n_tiles;             // tiles of the table (the single unit's range when n_units == 1)
   int* pending;            // per unit: this check needs the even-site pass (FINISH_ODD sets it)
   double* unit_sumTh_odd;  // per unit: odd-site part of the theta sum of the current check
   const int* unit_lat;     // lattice of each unit
-  const double* unit_vol;  // sites of each unit (Landau: V, Coulomb: Lx Ly Lz)
+  const double* unit_norm;  // per unit 1 / (nd Nc sites), 1 / (Nc sites): F and theta of Eqs. (1), (2)
   int* active;
   int* iters;
   const float2* part_F;    // per-tile partials as pairs (hi, lo)
@@ -262,8 +263,8 @@ struct FasdArgs {
   LatDev lat;
   void* kbuf;             // 4 complex fields, [f][t][z][y][x]
   char* gbuf;             // g(x): rows 0 and 1, 2 * 3 complex elements, planes [w][idx]
-  double* plane_F;        // per (z, t) plane
-  double* plane_th;
+  float2* plane_F;        // per (z, t) plane, as pairs (hi, lo)
+  float2* plane_th;
   const int* unit_planes; // n_units + 1 plane boundaries
   int* active;
   int* iters;
@@ -279,8 +280,18 @@ struct FasdArgs {
   int reunit;             // reunitarise the links in the update (single-step use)
   int mode;               // finish: FINISH_LOOP or FINISH_MEASURE
   int logL[4];
+  int kx;                 // kx columns per block of the z/t transform (power of 2, <= 8)
   double coef;            // alpha / 2 * p^2_max / N_fft
 };
+
+// kx columns per z/t-transform block: up to 8, halved until the block's columns
+// (nt x (KX Lz + 4) elements of c bytes) fit in 200 KB of shared memory
+inline int fasd_kx(const LatDev& lat, int nd, size_t c) {
+  int kx = lat.L[0] < 8 ? lat.L[0] : 8;
+  const size_t nt = nd == 4 ? lat.L[3] : 1;
+  while (kx > 1 && nt * ((size_t)kx * lat.L[2] + 4) * c > 200 * 1024) kx /= 2;
+  return kx;
+}
 
 // Differentiable F(c), theta(c) (kernels in gf_autograd.cuh)
 using c64 = cx<double>;
