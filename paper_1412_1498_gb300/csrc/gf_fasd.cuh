@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
 // ------------------------------------------------------------------------- C: FFT z(t), filter
 // Block: one field, one ky, KX consecutive kx (KX = a.kx <= 8, chosen on the host so the
 // block fits in shared memory) and (Coulomb) one t.  Shared layout
-// col[kxl + KX z + (KX Lz + 4) tl]: the pad keeps both transform directions free of bank
+// col[kxl + KX z + (KX Lz + KX) tl]: the pad keeps both transform directions free of bank
 // conflicts.
 template <class T, int ND>
 __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
   const int t0 = ND == 4 ? 0 : (int)blockIdx.z >> 2, nt = ND == 4 ? Lt : 1;
   if (ND == 3 && a.active && !a.active[t0]) return;
   cx<T>* col = reinterpret_cast<cx<T>*>(smraw);
-  const int pitch = KX * Lz + 4;
+  const int pitch = KX * Lz + KX;  // 2 pitch = 2 KX (Lz + 1): z-line groups split the banks evenly
   twiddles(twz, lz);
   if (ND == 4) twiddles(twt, a.logL[3]);
   for (int k = threadIdx.x; k < Lz; k += blockDim.x) {
@@ -424,8 +424,8 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
   const long long P = (long long)Lx * Ly;
   const int n = nt << (lz + lk);
   const int mz = Lz - 1, mk = KX - 1;
-#pragma unroll 8
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+#pragma unroll 16
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {  // 16 loads in flight per thread
     const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);
     col[kxl + KX * z + pitch * tl] = kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl];
   }
@@ -468,8 +468,8 @@ __global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_xy_inv_g(
   twiddles(twy, a.logL[1]);
   const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf);
   const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
-#pragma unroll 8
-  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+#pragma unroll 16
+  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {  // 16 loads in flight per thread
     const int f = i >> (a.logL[0] + a.logL[1]), j = i & (P - 1);
     pl[(f * Ly + (j >> a.logL[0])) * pitch + (j & (Lx - 1))] = kb[f * lat.V + plane0 + j];
   }
@@ -504,7 +504,6 @@ __global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
   const LatDev& lat = a.lat;
   const bool reunit_now = a.st ? state_reunit_sweep(a.st) : a.reunit != 0;
   char* base = a.links + lat.off_bytes;
-  // grid-stride over the sites (a small persistent grid: cheap when the loop is over)
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < lat.V;
        i += (long long)gridDim.x * blockDim.x) {
     const int p = i >= lat.Vh ? 1 : 0;

@@ -14,9 +14,15 @@ namespace gf {
 
 void launch_sweep_compact(int storage, int nd, const SweepArgs& a, int n_tiles, int threads,
                           cudaStream_t s) {
-#define GF_CALL(S, ND) k_or_sweep<S, ND, false><<<n_tiles, threads, 0, s>>>(a)
-  GF_COMPACT_SWITCH(storage, nd, GF_CALL)
+  if (a.form == GF_OR_FIRST_ORDER) {
+#define GF_CALL(S, ND) k_or_sweep<S, ND, false, GF_OR_FIRST_ORDER><<<n_tiles, threads, 0, s>>>(a)
+    GF_COMPACT_SWITCH(storage, nd, GF_CALL)
 #undef GF_CALL
+  } else {
+#define GF_CALL(S, ND) k_or_sweep<S, ND, false, GF_OR_EXACT><<<n_tiles, threads, 0, s>>>(a)
+    GF_COMPACT_SWITCH(storage, nd, GF_CALL)
+#undef GF_CALL
+  }
 }
 
 void launch_measure_compact(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,

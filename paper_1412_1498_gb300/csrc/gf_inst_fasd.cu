@@ -10,7 +10,7 @@ static size_t plane_smem(int storage, const LatDev& lat) {
 static size_t column_smem(int storage, int nd, const LatDev& lat) {
   const size_t c = storage == GF_FP64_18 ? 16 : 8;
   const int KX = fasd_kx(lat, nd, c);
-  return (size_t)(nd == 4 ? lat.L[3] : 1) * (lat.L[2] * KX + 4) * c;
+  return (size_t)(nd == 4 ? lat.L[3] : 1) * (lat.L[2] * KX + KX) * c;
 }
 
 // Shared-memory opt-in for every FA-SD kernel (outside any stream capture).
@@ -63,12 +63,7 @@ void launch_fasd_xy_inv_g(int storage, int nd, const FasdArgs& a, cudaStream_t s
 }
 
 void launch_fasd_update(int storage, int nd, const FasdArgs& a, cudaStream_t s) {
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (sms <= 0) sms = 1;
-  const long long want = (a.lat.V + 127) / 128, cap = 8LL * sms;  // 8 blocks of 128 per SM
-  const unsigned int nb = (unsigned int)(want < cap ? want : cap);
+  const unsigned int nb = (unsigned int)((a.lat.V + 127) / 128);  // one site per thread
 #define GF_CALL(S, T, ND) k_fasd_update<S, ND><<<nb, 128, 0, s>>>(a)
   GF_FASD_SWITCH(storage, nd, GF_CALL)
 #undef GF_CALL

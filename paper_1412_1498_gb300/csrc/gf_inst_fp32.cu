@@ -21,7 +21,12 @@ cudaError_t prepare_sweep_pipe() {
   if (dev >= kMaxDev) return cudaErrorInvalidDevice;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   for (int n = 0; n < 2; ++n) {
-    auto kern = n ? k_or_sweep_pipe<4> : k_or_sweep_pipe<3>;
+    // the grid is sized for the first-order kernel; the exact-power one takes the same
+    auto kern = n ? k_or_sweep_pipe<4, GF_OR_FIRST_ORDER> : k_or_sweep_pipe<3, GF_OR_FIRST_ORDER>;
+    auto kern_exact = n ? k_or_sweep_pipe<4, GF_OR_EXACT> : k_or_sweep_pipe<3, GF_OR_EXACT>;
+    e = cudaFuncSetAttribute(kern_exact, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(2 * kPipeWords * 256 * sizeof(float4)));
+    if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(2 * kPipeWords * 256 * sizeof(float4)));
     if (e != cudaSuccess) return e;
@@ -64,19 +69,28 @@ void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads
   if (grid <= 0) grid = 1;
   if (grid > n_tiles) grid = n_tiles;
   const size_t smem = 2 * kPipeWords * threads * sizeof(float4);
-  if (nd == 4) k_or_sweep_pipe<4><<<grid, threads, smem, s>>>(a);
-  else k_or_sweep_pipe<3><<<grid, threads, smem, s>>>(a);
+  if (a.form == GF_OR_FIRST_ORDER) {
+    if (nd == 4) k_or_sweep_pipe<4, GF_OR_FIRST_ORDER><<<grid, threads, smem, s>>>(a);
+    else k_or_sweep_pipe<3, GF_OR_FIRST_ORDER><<<grid, threads, smem, s>>>(a);
+  } else {
+    if (nd == 4) k_or_sweep_pipe<4, GF_OR_EXACT><<<grid, threads, smem, s>>>(a);
+    else k_or_sweep_pipe<3, GF_OR_EXACT><<<grid, threads, smem, s>>>(a);
+  }
 }
 
 void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int threads,
                        cudaStream_t s) {
-  if (storage == GF_FP32_12) {
-    if (nd == 4) k_or_sweep<GF_FP32_12, 4, false><<<n_tiles, threads, 0, s>>>(a);
-    else k_or_sweep<GF_FP32_12, 3, false><<<n_tiles, threads, 0, s>>>(a);
+#define GF_CALL(S, F)                                                          \
+  if (nd == 4) k_or_sweep<S, 4, false, F><<<n_tiles, threads, 0, s>>>(a);      \
+  else k_or_sweep<S, 3, false, F><<<n_tiles, threads, 0, s>>>(a);
+  if (a.form == GF_OR_FIRST_ORDER) {
+    if (storage == GF_FP32_12) { GF_CALL(GF_FP32_12, GF_OR_FIRST_ORDER) }
+    else { GF_CALL(GF_FP32_18, GF_OR_FIRST_ORDER) }
   } else {
-    if (nd == 4) k_or_sweep<GF_FP32_18, 4, false><<<n_tiles, threads, 0, s>>>(a);
-    else k_or_sweep<GF_FP32_18, 3, false><<<n_tiles, threads, 0, s>>>(a);
+    if (storage == GF_FP32_12) { GF_CALL(GF_FP32_12, GF_OR_EXACT) }
+    else { GF_CALL(GF_FP32_18, GF_OR_EXACT) }
   }
+#undef GF_CALL
 }
 
 void launch_measure_fp32(int storage, int nd, const MeasureArgs& a, int n_tiles, int threads,

@@ -4,8 +4,13 @@
 namespace gf {
 
 void launch_sweep_fp64(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s) {
-  if (nd == 4) k_or_sweep<GF_FP64_18, 4, false><<<n_tiles, threads, 0, s>>>(a);
-  else k_or_sweep<GF_FP64_18, 3, false><<<n_tiles, threads, 0, s>>>(a);
+  if (a.form == GF_OR_FIRST_ORDER) {
+    if (nd == 4) k_or_sweep<GF_FP64_18, 4, false, GF_OR_FIRST_ORDER><<<n_tiles, threads, 0, s>>>(a);
+    else k_or_sweep<GF_FP64_18, 3, false, GF_OR_FIRST_ORDER><<<n_tiles, threads, 0, s>>>(a);
+  } else {
+    if (nd == 4) k_or_sweep<GF_FP64_18, 4, false, GF_OR_EXACT><<<n_tiles, threads, 0, s>>>(a);
+    else k_or_sweep<GF_FP64_18, 3, false, GF_OR_EXACT><<<n_tiles, threads, 0, s>>>(a);
+  }
 }
 
 void launch_measure_fp64(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s) {

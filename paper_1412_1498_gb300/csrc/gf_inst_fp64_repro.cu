@@ -6,8 +6,13 @@
 namespace gf {
 
 void launch_sweep_fp64_repro(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s) {
-  if (nd == 4) k_or_sweep<GF_FP64_18, 4, true><<<n_tiles, threads, 0, s>>>(a);
-  else k_or_sweep<GF_FP64_18, 3, true><<<n_tiles, threads, 0, s>>>(a);
+  if (a.form == GF_OR_FIRST_ORDER) {
+    if (nd == 4) k_or_sweep<GF_FP64_18, 4, true, GF_OR_FIRST_ORDER><<<n_tiles, threads, 0, s>>>(a);
+    else k_or_sweep<GF_FP64_18, 3, true, GF_OR_FIRST_ORDER><<<n_tiles, threads, 0, s>>>(a);
+  } else {
+    if (nd == 4) k_or_sweep<GF_FP64_18, 4, true, GF_OR_EXACT><<<n_tiles, threads, 0, s>>>(a);
+    else k_or_sweep<GF_FP64_18, 3, true, GF_OR_EXACT><<<n_tiles, threads, 0, s>>>(a);
+  }
 }
 
 }  // namespace gf

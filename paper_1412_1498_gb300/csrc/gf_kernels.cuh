@@ -24,9 +24,9 @@ __device__ __forceinline__ double gf_rsqrt<double>(double x) { return rsqrt(x); 
 template <>
 __device__ __forceinline__ float gf_rsqrt<float>(float x) { return rsqrtf(x); }
 
-template <class T, bool REPRO>
+template <class T, bool REPRO, int FORM>
 __device__ __forceinline__ void su2_maximiser(const cx<T> (&K)[9], int i, int j, T omega,
-                                              int form, cx<T>& a, cx<T>& b) {
+                                              cx<T>& a, cx<T>& b) {
   const cx<T> alpha = cadd(K[3 * i + i], cconj(K[3 * j + j]));
   const cx<T> beta = csub(K[3 * j + i], cconj(K[3 * i + j]));
   const T n2 = ((alpha.re * alpha.re + alpha.im * alpha.im) + beta.re * beta.re) + beta.im * beta.im;
@@ -45,7 +45,7 @@ __device__ __forceinline__ void su2_maximiser(const cx<T> (&K)[9], int i, int j,
       b = {beta.re * rn, -beta.im * rn};
     }
   }
-  if (form == GF_OR_FIRST_ORDER) {
+  if constexpr (FORM == GF_OR_FIRST_ORDER) {
     // g^omega to first order: 1 + omega (g - 1), renormalised onto SU(2)
     const cx<T> a1 = {(T(1) - omega) + omega * a.re, omega * a.im};
     const cx<T> b1 = {omega * b.re, omega * b.im};
@@ -90,10 +90,10 @@ __device__ __forceinline__ void su2_left_mul(cx<T> (&M)[9], int i, int j, cx<T> 
 // (0,2), (1,2)), K rotated after each one.
 // The first product R1 * 1 is R1 itself and K is not needed after the third step; both
 // shortcuts give the values of the plain sequence (x * 1 = x, x + 0 = x).
-template <class T, bool REPRO>
-__device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega, int form) {
+template <class T, bool REPRO, int FORM>
+__device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega) {
   cx<T> a, b;
-  su2_maximiser<T, REPRO>(K, 0, 1, omega, form, a, b);
+  su2_maximiser<T, REPRO, FORM>(K, 0, 1, omega, a, b);
   su2_left_mul(K, 0, 1, a, b);
 #pragma unroll
   for (int e = 0; e < 9; ++e) G[e] = {T(0), T(0)};
@@ -102,10 +102,10 @@ __device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega
   G[3] = cneg(cconj(b));
   G[4] = cconj(a);
   G[8] = {T(1), T(0)};
-  su2_maximiser<T, REPRO>(K, 0, 2, omega, form, a, b);
+  su2_maximiser<T, REPRO, FORM>(K, 0, 2, omega, a, b);
   su2_left_mul(K, 0, 2, a, b);
   su2_left_mul(G, 0, 2, a, b);
-  su2_maximiser<T, REPRO>(K, 1, 2, omega, form, a, b);
+  su2_maximiser<T, REPRO, FORM>(K, 1, 2, omega, a, b);
   su2_left_mul(G, 1, 2, a, b);
 }
 
@@ -285,11 +285,11 @@ struct FasdArgs {
 };
 
 // kx columns per z/t-transform block: up to 8, halved until the block's columns
-// (nt x (KX Lz + 4) elements of c bytes) fit in 200 KB of shared memory
+// (nt x (KX Lz + KX) elements of c bytes) fit in 200 KB of shared memory
 inline int fasd_kx(const LatDev& lat, int nd, size_t c) {
   int kx = lat.L[0] < 8 ? lat.L[0] : 8;
   const size_t nt = nd == 4 ? lat.L[3] : 1;
-  while (kx > 1 && nt * ((size_t)kx * lat.L[2] + 4) * c > 200 * 1024) kx /= 2;
+  while (kx > 1 && nt * ((size_t)kx * lat.L[2] + kx) * c > 200 * 1024) kx /= 2;
   return kx;
 }
 
@@ -314,7 +314,7 @@ struct AdArgs {
 // Algorithm 1, one half-sweep: every site of one parity, one thread per site.
 // KEEP: hold the 8 links in registers (FP32); otherwise stream them twice (FP64).
 // ----------------------------------------------------------------------------------
-template <int S, int ND, bool REPRO>
+template <int S, int ND, bool REPRO, int FORM>
 __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   using St = Store<S>;
   using T = typename St::T;
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
       }
 #pragma unroll
       for (int mu = 0; mu < ND; ++mu) add_to_K(K, f[mu], b[mu]);
-      su3_update<T, REPRO>(K, G, omega, a.form);
+      su3_update<T, REPRO, FORM>(K, G, omega);
       cx<T> A[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
         St::load(base, V, mu, idx_b[mu], b);
         add_to_K(K, f, b);
       }
-      su3_update<T, REPRO>(K, G, omega, a.form);
+      su3_update<T, REPRO, FORM>(K, G, omega);
       cx<T> A[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};

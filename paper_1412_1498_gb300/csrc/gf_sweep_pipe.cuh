@@ -75,7 +75,7 @@ __device__ __forceinline__ void pipe_read(const float4* slot, int B, int word0, 
   }
 }
 
-template <int ND>
+template <int ND, int FORM>
 __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
   extern __shared__ float4 sm[];
   __shared__ double red[64];
@@ -114,7 +114,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
           pipe_read(slot, B, 12 + 3 * mu, b);
           add_to_K(K, f, b);
         }
-        su3_update<float, false>(K, G, omega, a.form);
+        su3_update<float, false, FORM>(K, G, omega);
         cx<float> A[9];
 #pragma unroll
         for (int e = 0; e < 9; ++e) A[e] = {0.f, 0.f};
