@@ -43,6 +43,12 @@ V = DIMS[0] * DIMS[1] * DIMS[2] * DIMS[3]
 STEP_BYTES = 16 * V * LINK_B
 CHECK_BYTES = 4 * V * LINK_B
 HALF_SWEEP_BYTES = 8 * V * LINK_B
+# FP32 flops of one FP32-12 site update (an FMA counts 2): K from 8 links with their third
+# rows rebuilt, 480; three subgroup maximisers with first-order overrelaxation, 102; two
+# rotations of K and two of G (the first subgroup is written into G), 336; G applied to
+# the 8 links, 1224 (4 third rows + 6 x 3 complex MACs per forward link, 6 x 3 per
+# backward link)
+FLOP_PER_SITE = 2142
 WORKLOAD = "landau-32^4-fp32-12: OR sweep (even+odd, omega 1.7, reunit every 20) + F/theta stop check"
 
 
@@ -332,7 +338,7 @@ def run_gpu(args):
         p1.record(stream)
         p1.synchronize()
         split_probe = {"sweeps": args.split_probe, "ms_per_sweep_incl_conversions": p0.elapsed_time(p1) / args.split_probe,
-                       "link_bytes_per_sweep": 20 * V * 144}
+                       "link_bytes_per_sweep": 16 * V * 144}
         f3.close()
         del f3
 
@@ -391,7 +397,9 @@ def run_gpu(args):
                 "kernel": "k_or_sweep_pipe<Landau> (FP32-12)" if best[1] == gf.GF_SWEEP_PIPELINED
                 else "k_or_sweep<FP32_12, Landau>",
                 "bytes_per_launch": HALF_SWEEP_BYTES, "ms_per_launch": half_ms,
-                "peak_kind": f"{peak_kind} HBM copy bandwidth"}
+                "peak_kind": f"{peak_kind} HBM copy bandwidth",
+                "fp32_tflops": FLOP_PER_SITE * (V // 2) / (half_ms * 1e-3) / 1e12,
+                "flop_per_site_update": FLOP_PER_SITE}
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
