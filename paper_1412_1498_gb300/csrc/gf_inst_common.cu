@@ -35,6 +35,21 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   const bool pend_in = a.pending[u] != 0;
   const int tb = a.n_units == 1 ? 0 : a.unit_tiles[u];
   const int te = a.n_units == 1 ? a.n_tiles : a.unit_tiles[u + 1];
+  // The first pass of tile partials: with one unit its range is a kernel argument, so
+  // these loads wait for nothing and travel with the ones above.  (FINISH_LOOP, which
+  // mostly has nothing to add, loads inside the reduction.)
+  const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET;
+  const bool early = a.mode != FINISH_LOOP;
+  const float2* p1 = a.mode == FINISH_ODD ? a.part_th_odd : a.part_th_even;
+  float2 x0[kFinishUnroll], x1[kFinishUnroll], x2[kFinishUnroll];
+#pragma unroll
+  for (int j = 0; j < kFinishUnroll; ++j) {
+    const int i = tb + tid + j * kFinishThreads;
+    const bool in = early && i < te;
+    x0[j] = in ? a.part_F[i] : make_float2(0.f, 0.f);
+    x1[j] = in ? p1[i] : make_float2(0.f, 0.f);
+    x2[j] = in && outside ? a.part_th_odd[i] : make_float2(0.f, 0.f);
+  }
   // what thread 0 needs after the reduction
   double invF = 0.0, invT = 0.0, uF_old = 0.0, uT_old = 0.0, uTo = 0.0;
   if (tid == 0) {
@@ -59,26 +74,31 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   else if (a.mode == FINISH_LOOP) reduce = check && was_active && pend_in;
   else reduce = true;
   if (reduce) {
-    const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET;
-    const float2* p1 = a.mode == FINISH_ODD ? a.part_th_odd : a.part_th_even;
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0;
-    // kFinishUnroll tiles per thread and pass: all their loads are in flight together
+    // kFinishUnroll tiles per thread and pass, all loads of a pass in flight together,
+    // added as a fixed binary tree
     for (int i0 = tb + tid; i0 < te; i0 += kFinishUnroll * kFinishThreads) {
-      float2 x0[kFinishUnroll], x1[kFinishUnroll], x2[kFinishUnroll];
+      if (i0 != tb + tid || !early) {
 #pragma unroll
-      for (int j = 0; j < kFinishUnroll; ++j) {
-        const int i = i0 + j * kFinishThreads;
-        const bool in = i < te;
-        x0[j] = in && a.mode != FINISH_LOOP ? a.part_F[i] : make_float2(0.f, 0.f);
-        x1[j] = in ? p1[i] : make_float2(0.f, 0.f);
-        x2[j] = in && outside ? a.part_th_odd[i] : make_float2(0.f, 0.f);
+        for (int j = 0; j < kFinishUnroll; ++j) {
+          const int i = i0 + j * kFinishThreads;
+          const bool in = i < te;
+          x0[j] = in && a.mode != FINISH_LOOP ? a.part_F[i] : make_float2(0.f, 0.f);
+          x1[j] = in ? p1[i] : make_float2(0.f, 0.f);
+          x2[j] = in && outside ? a.part_th_odd[i] : make_float2(0.f, 0.f);
+        }
       }
 #pragma unroll
-      for (int j = 0; j < kFinishUnroll; ++j) {
-        acc0 = pair_add(acc0, x0[j]);
-        acc1 = pair_add(acc1, x1[j]);
-        acc2 = pair_add(acc2, x2[j]);
-      }
+      for (int w = kFinishUnroll / 2; w > 0; w >>= 1)
+#pragma unroll
+        for (int j = 0; j < w; ++j) {
+          x0[j] = pair_add(x0[j], x0[j + w]);
+          x1[j] = pair_add(x1[j], x1[j + w]);
+          x2[j] = pair_add(x2[j], x2[j + w]);
+        }
+      acc0 = pair_add(acc0, x0[0]);
+      acc1 = pair_add(acc1, x1[0]);
+      acc2 = pair_add(acc2, x2[0]);
     }
     red[0][tid] = acc0;
     red[1][tid] = acc1;
