@@ -277,6 +277,22 @@ GF_API int gf_set_sweeps_done(gf_handle *h, int n);
 GF_API int gf_fix_phase_sweeps(const gf_handle *h, int *fp32_sweeps, int *fp64_sweeps);
 
 /*
+ * Convergence history of gf_fix (Algorithm 1 computes theta after every sweep).
+ *   buf: device memory (or host memory mapped for the device) for `capacity` records of
+ *   1 + 2 * n_lat doubles: the sweep number within the gf_fix call (0 = the field before
+ *   the first sweep), then F and theta of every lattice (Eqs. (1)-(3); for Coulomb gauge
+ *   the totals over the slices).  One record per check sweep (gf_set_check_interval);
+ *   records beyond `capacity` are dropped.  While a history is set every check measures
+ *   theta in full (the loop otherwise skips the even-site part where the odd-site part
+ *   alone decides the stop), so sweeps are slower.  capacity = 0 (or buf = NULL with
+ *   capacity 0) turns it off.  The caller owns buf and keeps it alive while it is set.
+ *   Overrelaxation only (not the Fourier-accelerated loop).
+ *   gf_history_count: records written by the last gf_fix.
+ */
+GF_API int gf_set_history(gf_handle *h, double *buf, int capacity);
+GF_API int gf_history_count(const gf_handle *h, int *n);
+
+/*
  * F and theta of a field held in device memory, with no allocation of any kind.
  *
  * The paper has no counterpart to this call; it exists for callers that cannot

@@ -1,11 +1,12 @@
 // gf_api.cu -- host implementation of the C ABI declared in include/gf.h.
 //
-// Algorithm 1 of the paper as a device-driven loop: each sweep is four launches
-// (even half-sweep, odd half-sweep with fused reunitarisation and odd-site theta,
-// even-site F/theta pass, finishing reduction) that read and update a small DevState
-// in device memory, so that a captured CUDA graph of many sweeps needs no host
-// decision between them.  The host synchronises once per graph replay to read the
-// number of still-active convergence units.
+// Algorithm 1 of the paper as a device-driven loop: each sweep is five launches (even
+// half-sweep; odd half-sweep with fused reunitarisation, F and odd-site theta; the
+// odd-part finish, which decides every unit whose odd-site theta alone reaches eps;
+// the even-site theta pass for the undecided units; the loop finish) that read and
+// update a small DevState in device memory, so that a captured CUDA graph of many
+// sweeps needs no host decision between them.  The host synchronises once per graph
+// replay to read the number of still-active convergence units.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -278,6 +279,8 @@ struct gf_handle {
   float2 *d_partF = nullptr, *d_pthe = nullptr, *d_ptho = nullptr;  // per-tile pairs (hi, lo)
   double* d_usTo = nullptr;
   int* d_pending = nullptr;
+  double* hist = nullptr;  // caller's device buffer of check records (gf_set_history)
+  int hist_cap = 0, hist_n = 0, hist_sweeps = 0;
   double* d_unit_norm = nullptr;
   double *d_usF = nullptr, *d_usT = nullptr, *d_uF = nullptr, *d_uT = nullptr, *d_lF = nullptr,
          *d_lT = nullptr;
@@ -437,6 +440,8 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   a.part_th_odd = h->d_ptho;
   a.pending = h->d_pending;
   a.unit_sumTh_odd = h->d_usTo;
+  a.hist = h->hist;
+  a.hist_cap = h->hist_cap;
   a.unit_sumF = h->d_usF;
   a.unit_sumTh = h->d_usT;
   a.unit_F = h->d_uF;
@@ -523,6 +528,8 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   s.n_active = 0;
   s.ticket = 0;
   s.eps = eps;
+  s.hist_n = h->hist_n;
+  s.hist_base = h->hist_sweeps - offset;
   GF_CK(h, cudaMemcpyAsync(h->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream));
   int rc = enqueue_measure_all(h, FINISH_RESET);
   if (rc != GF_OK) return rc;
@@ -533,6 +540,7 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
   }
   *done = s.sweep - offset;
+  h->hist_n = s.hist_n;
   return GF_OK;
 }
 
@@ -923,6 +931,8 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
   if (!(eps > 0.0) || maxiter < 0) return fail(h, GF_EINVAL, "need eps > 0 and maxiter >= 0");
   GF_CK(h, cudaMemsetAsync(h->d_iters, 0, sizeof(int) * h->n_units, h->stream));
   h->phase_sweeps[0] = h->phase_sweeps[1] = 0;
+  h->hist_n = 0;
+  h->hist_sweeps = 0;
   int rc, done = 0;
   if (h->method == GF_METHOD_FASD) {
     if (!(h->flags & GF_FLAG_FASD)) return fail(h, GF_ESTATE, "create the handle with GF_FLAG_FASD for Fourier acceleration");
@@ -949,6 +959,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
       }
       h->cur = 2;
       h->sweeps_done = 0;
+      h->hist_sweeps = done;
       rc = run_phase(h, eps, maxiter - done, &done2);
       for (int l = 0; l < h->n_lat; ++l) {
         launch_split_to_fp64(h->links64, h->lats64[l], h->stream);
@@ -966,6 +977,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
     }
     int done3 = 0;
     h->sweeps_done = 0;
+    h->hist_sweeps = done;
     if ((rc = run_phase(h, eps, maxiter - done, &done3)) != GF_OK) return rc;
     h->sweeps_done = done3;
     h->phase_sweeps[1] = done2 + done3;
@@ -1194,6 +1206,23 @@ int gf_fix_phase_sweeps(const gf_handle* h, int* fp32_sweeps, int* fp64_sweeps) 
   if (!h) return GF_EINVAL;
   if (fp32_sweeps) *fp32_sweeps = h->phase_sweeps[0];
   if (fp64_sweeps) *fp64_sweeps = h->phase_sweeps[1];
+  return GF_OK;
+}
+
+int gf_set_history(gf_handle* h, double* buf, int capacity) {
+  if (!h) return GF_EINVAL;
+  if (capacity < 0 || (capacity > 0 && buf == nullptr)) return fail(h, GF_EINVAL, "history needs a buffer for capacity > 0 records");
+  if (buf && ((uintptr_t)buf % 8) != 0) return fail(h, GF_EINVAL, "history buffer must be 8-byte aligned");
+  h->hist = capacity > 0 ? buf : nullptr;
+  h->hist_cap = capacity > 0 ? capacity : 0;
+  h->hist_n = 0;
+  drop_graphs(h);  // the finishing kernels of the captured loop carry the buffer
+  return GF_OK;
+}
+
+int gf_history_count(const gf_handle* h, int* n) {
+  if (!h || !n) return GF_EINVAL;
+  *n = h->hist_n;
   return GF_OK;
 }
 

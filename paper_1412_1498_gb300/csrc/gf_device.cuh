@@ -62,6 +62,8 @@ struct DevState {
   int stop;             // Fourier-accelerated loop: final field measured, nothing left to do
   int need_exact;       // this check sweep has units whose odd-site theta alone is below eps
   int sweep_closed;     // the odd-part finish already counted this sweep (nothing pending)
+  int hist_n;           // history records written in the current gf_fix
+  int hist_base;        // sweep number of the record = hist_base + sweep (across phases)
   double eps;           // stop threshold of the current phase
 };
 

@@ -19,6 +19,20 @@ namespace gf {
 // sweep's bookkeeping and closes it; otherwise the even-site pass runs for the pending
 // units and LOOP completes their theta and masks, counts the sweep and updates the
 // loop state.
+// One history record: the sweep number, then F and theta of every lattice (lattice totals
+// already written); by one thread.
+__device__ __forceinline__ void history_record(const FinishArgs& a, int sweep_no) {
+  const int n = a.st->hist_n;
+  if (n >= a.hist_cap) return;
+  double* r = a.hist + (size_t)n * (1 + 2 * a.n_lat);
+  r[0] = (double)sweep_no;
+  for (int l = 0; l < a.n_lat; ++l) {
+    r[1 + 2 * l] = __ldcg(a.lat_F + l);
+    r[2 + 2 * l] = __ldcg(a.lat_theta + l);
+  }
+  a.st->hist_n = n + 1;
+}
+
 __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   __shared__ float2 red[3][kFinishThreads];
   __shared__ int s_last;
@@ -128,7 +142,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
         a.unit_sumF[u] = s0;
         a.unit_F[u] = s0 * invF;
         a.unit_sumTh_odd[u] = s1;
-        pend = forced || !(s1 * invT >= eps);
+        pend = forced || a.hist != nullptr || !(s1 * invT >= eps);  // a history wants every theta
       }
       a.pending[u] = pend;
     } else {
@@ -167,6 +181,8 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
           a.st->n_active = act ? 1 : 0;
         }
         if (loop) a.st->sweep = sweep + 1;
+        if (a.hist && ((a.mode == FINISH_LOOP && check) || (a.mode == FINISH_RESET && a.st->hist_n == 0)))
+          history_record(a, a.mode == FINISH_LOOP ? a.st->hist_base + sweep + 1 : 0);
       }
       a.st->ticket = 0u;
       s_last = 0;
@@ -211,6 +227,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
       a.lat_theta[l] = sTh * (1.0 / (3.0 * (double)lat.V));
     }
   }
+  __syncthreads();  // lattice totals written by other threads of this block
   if (tid == 0) {
     if (a.mode == FINISH_ODD) {
       a.st->need_exact = 0;
@@ -218,6 +235,8 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
     } else if (a.mode != FINISH_MEASURE) {
       a.st->n_active = n;
     }
+    if (a.hist && ((a.mode == FINISH_LOOP && check) || (a.mode == FINISH_RESET && a.st->hist_n == 0)))
+      history_record(a, a.mode == FINISH_LOOP ? a.st->hist_base + sweep + 1 : 0);
     if (loop) a.st->sweep += 1;
     a.st->ticket = 0u;
   }

@@ -234,6 +234,8 @@ struct FinishArgs {
   const int* unit_tiles;   // n_units + 1 tile boundaries
   int n_tiles;             // tiles of the table (the single unit's range when n_units == 1)
   int* pending;            // per unit: this check needs the even-site pass (FINISH_ODD sets it)
+  double* hist;            // nullable: records (sweep, F and theta of every lattice) of each check
+  int hist_cap;            // records hist can hold
   double* unit_sumTh_odd;  // per unit: odd-site part of the theta sum of the current check
   const int* unit_lat;     // lattice of each unit
   const double* unit_norm;  // per unit 1 / (nd Nc sites), 1 / (Nc sites): F and theta of Eqs. (1), (2)

@@ -70,6 +70,8 @@ _SIGS = {
     "gf_autotune": (_int, [_vp, _IP, _IP]),
     "gf_get_sweeps_done": (_int, [_vp, _IP]),
     "gf_set_sweeps_done": (_int, [_vp, _int]),
+    "gf_set_history": (_int, [_vp, _vp, _int]),
+    "gf_history_count": (_int, [_vp, _IP]),
     "gf_fa_sd_step": (_int, [_vp, _dbl]),
     "gf_set_method": (_int, [_vp, _int]),
     "gf_set_alpha": (_int, [_vp, _dbl]),
@@ -256,6 +258,16 @@ def gf_set_sweeps_done(h, n: int) -> None:
     _check(_lib.gf_set_sweeps_done(h, n), h)
 
 
+def gf_set_history(h, buf_ptr: int, capacity: int) -> None:
+    _check(_lib.gf_set_history(h, ctypes.c_void_p(buf_ptr), capacity), h)
+
+
+def gf_history_count(h) -> int:
+    n = ctypes.c_int()
+    _check(_lib.gf_history_count(h, ctypes.byref(n)), h)
+    return n.value
+
+
 def gf_fix_phase_sweeps(h):
     a, b = ctypes.c_int(), ctypes.c_int()
     _check(_lib.gf_fix_phase_sweeps(h, ctypes.byref(a), ctypes.byref(b)), h)
@@ -331,6 +343,22 @@ class GaugeFixer:
     def or_sweep(self, parity: int = 2, omega: float = 1.7):
         gf_or_sweep(self.h, parity, omega)
 
-    def fix(self, eps: float, maxiter: int):
-        rc, it, F, th = gf_fix(self.h, eps, maxiter)
-        return dict(rc=rc, iters=it, F=F, theta=th, phase_sweeps=gf_fix_phase_sweeps(self.h))
+    def fix(self, eps: float, maxiter: int, history: int = 0):
+        """gf_fix; history > 0 also returns up to that many records (sweep, then F and
+        theta of every lattice) of the checks, as an array under "history"."""
+        buf = None
+        if history > 0:
+            import torch
+            buf = torch.zeros((history, 1 + 2 * len(self.dims_list)), dtype=torch.float64,
+                              device=self.device)
+            gf_set_history(self.h, buf.data_ptr(), history)
+        try:
+            rc, it, F, th = gf_fix(self.h, eps, maxiter)
+            out = dict(rc=rc, iters=it, F=F, theta=th, phase_sweeps=gf_fix_phase_sweeps(self.h))
+            if buf is not None:
+                n = gf_history_count(self.h)
+                out["history"] = buf[:n].cpu().numpy()
+        finally:
+            if buf is not None:
+                gf_set_history(self.h, 0, 0)
+        return out

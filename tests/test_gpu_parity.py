@@ -201,6 +201,44 @@ def test_stop_rule_with_check_interval(gf, k):
     fx.close()
 
 
+def test_theta_history_matches_oracle(gf):
+    # gf_set_history: one record per check (sweep, F, theta), theta measured in full
+    dims = (8, 8, 8, 8)
+    U = fields.random_gauge_config(dims, 0.4, 1, 2)
+    r = oracle.fix(U.copy(), 1e-12, 500, 1.7)
+    fx = make(gf, dims, gf.GF_LANDAU, gf.GF_FP64_18, repro=True)
+    fx.upload(U)
+    out = fx.fix(1e-12, 500, history=1000)
+    h = out["history"]
+    n = int(r["iters"])
+    assert out["iters"][0] == n and h.shape == (n + 1, 3)
+    assert np.array_equal(h[:, 0], np.arange(n + 1))
+    assert np.allclose(h[:, 2], r["theta_hist"], rtol=1e-12, atol=0)
+    assert h[-1, 1] == out["F"][0] and h[-1, 2] == out["theta"][0]
+    # check interval 7: the initial field, every 7th sweep, the budget's last sweep
+    gf.gf_set_check_interval(fx.h, 7)
+    fx.upload(U)
+    out = fx.fix(1e-300, 30, history=100)
+    assert np.array_equal(out["history"][:, 0], [0, 7, 14, 21, 28, 30])
+    assert np.allclose(out["history"][:, 2], r["theta_hist"][[0, 7, 14, 21, 28, 30]], rtol=1e-12, atol=0)
+    # a short buffer keeps the first records
+    fx.upload(U)
+    out = fx.fix(1e-300, 30, history=3)
+    assert np.array_equal(out["history"][:, 0], [0, 7, 14])
+    fx.close()
+    # mixed precision: the records run on across the FP32 and FP64 phases
+    fm = make(gf, dims, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True)
+    fm.upload(U)
+    out = fm.fix(1e-15, 3000, history=4000)
+    h = out["history"]
+    assert h.shape[0] == out["iters"][0] + 1
+    assert np.array_equal(h[:, 0], np.arange(h.shape[0]))
+    n32 = out["phase_sweeps"][0]
+    assert h[n32, 2] < 1e-8 <= h[n32 - 1, 2]      # the switch to FP64 at theta < 1e-8
+    assert h[-1, 2] < 1e-15 <= h[-2, 2]
+    fm.close()
+
+
 # ---------------------------------------------------------------- FP32 storage
 @pytest.mark.parametrize("storage", [1, 2])
 @pytest.mark.parametrize("gauge", [0, 1])
