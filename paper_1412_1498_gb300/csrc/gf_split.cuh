@@ -96,6 +96,23 @@ __device__ __forceinline__ void split_store(char* base, long long V, int mu, int
 #pragma unroll
   for (int w = 0; w < 9; ++w) p[(long long)(w * 4 + mu) * V + idx] = make_float4(u[w].re.hi, u[w].im.hi, u[w].re.lo, u[w].im.lo);
 }
+// Apply phase: the reload of a link is the last use of its line and the store streams
+// out (cache hints ld.global.lu / st.global.cs), so the updated links do not evict the
+// lines that other blocks loaded for their K phase and will reload: 0.537 -> 0.495 ms
+// per 32^4 polish sweep.
+__device__ __forceinline__ void split_load_last(const char* base, long long V, int mu, int idx, csf (&u)[9]) {
+  const float4* p = reinterpret_cast<const float4*>(base);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) {
+    const float4 v = __ldlu(p + (long long)(w * 4 + mu) * V + idx);
+    u[w] = {{v.x, v.z}, {v.y, v.w}};
+  }
+}
+__device__ __forceinline__ void split_store_stream(char* base, long long V, int mu, int idx, const csf (&u)[9]) {
+  float4* p = reinterpret_cast<float4*>(base);
+#pragma unroll
+  for (int w = 0; w < 9; ++w) __stcs(p + (long long)(w * 4 + mu) * V + idx, make_float4(u[w].re.hi, u[w].im.hi, u[w].re.lo, u[w].im.lo));
+}
 __device__ __forceinline__ csf split_of(double re, double im) {
   const float rh = (float)re, ih = (float)im;
   return {{rh, (float)(re - (double)rh)}, {ih, (float)(im - (double)ih)}};
@@ -332,7 +349,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
       for (int side = 0; side < 2; ++side) {
         const int idx = side == 0 ? idx_f : idx_b[mu];
         csf u[9];
-        split_load(base, V, mu, idx, u);
+        split_load_last(base, V, mu, idx, u);
         cx<float> du[9];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -358,7 +375,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
           }
           tr[side] = sf_f(u[0].re) + sf_f(u[4].re) + sf_f(u[8].re);
         }
-        split_store(base, V, mu, idx, u);
+        split_store_stream(base, V, mu, idx, u);
       }
       if (mu < ND && measure_now) fsum = fsum + (tr[0] + tr[1]);
     }
