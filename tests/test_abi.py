@@ -53,3 +53,38 @@ def test_bad_enums_rejected():
         assert e.value.code == gf.GF_EINVAL
     with pytest.raises(gf.GFError):
         gf.gf_workspace_bytes([(4, 4, 4, 4)], gf.GF_LANDAU, gf.GF_FP32_12, flags=8)
+
+
+def test_workspace_scales_with_link_storage():
+    # links dominate the workspace: 8, 12 or 18 reals in FP32 or FP64
+    V = 32 ** 4
+    sizes = {st: gf.gf_workspace_bytes([(32, 32, 32, 32)], gf.GF_LANDAU, st)
+             for st in (gf.GF_FP32_8, gf.GF_FP32_12, gf.GF_FP32_18, gf.GF_FP64_8, gf.GF_FP64_12, gf.GF_FP64_18)}
+    per_link = {gf.GF_FP32_8: 32, gf.GF_FP32_12: 48, gf.GF_FP32_18: 72, gf.GF_FP64_8: 64,
+                gf.GF_FP64_12: 96, gf.GF_FP64_18: 144}
+    base = sizes[gf.GF_FP32_12] - 4 * V * 48
+    for st, b in sizes.items():
+        assert b - 4 * V * per_link[st] == base, st
+    # mixed precision keeps an FP64-18 copy only for the FP32 storages
+    for st in (gf.GF_FP32_8, gf.GF_FP32_12, gf.GF_FP32_18):
+        assert gf.gf_workspace_bytes([(32, 32, 32, 32)], gf.GF_LANDAU, st, gf.GF_FLAG_MIXED) - sizes[st] >= 4 * V * 144
+    for st in (gf.GF_FP64_8, gf.GF_FP64_12, gf.GF_FP64_18):
+        assert gf.gf_workspace_bytes([(32, 32, 32, 32)], gf.GF_LANDAU, st, gf.GF_FLAG_MIXED) == sizes[st]
+
+
+def test_creation_limits():
+    # site coordinates are divided by Lx and Ly with 32-bit reciprocals: Lx Ly Lz max(Lx, Ly) < 2^32
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_workspace_bytes([(2048, 2048, 2, 2)], gf.GF_LANDAU, gf.GF_FP32_12)
+    assert e.value.code == gf.GF_EINVAL
+    # Fourier acceleration: one lattice, FP32-12 or FP64-18, power-of-two transformed extents
+    for dims, st in [((6, 8, 8, 8), gf.GF_FP32_12), ((8, 8, 8, 8), gf.GF_FP32_8), ((8, 8, 8, 8), gf.GF_FP64_12)]:
+        with pytest.raises(gf.GFError) as e:
+            gf.gf_workspace_bytes([dims], gf.GF_LANDAU, st, gf.GF_FLAG_FASD)
+        assert e.value.code == gf.GF_EINVAL
+    assert gf.gf_workspace_bytes([(8, 8, 8, 6)], gf.GF_COULOMB, gf.GF_FP32_12, gf.GF_FLAG_FASD) > 0
+    with pytest.raises(gf.GFError):
+        gf.gf_workspace_bytes([(8, 8, 8, 8)] * 2, gf.GF_LANDAU, gf.GF_FP32_12, gf.GF_FLAG_FASD)
+    # the differentiable functional: one FP64-18 lattice
+    with pytest.raises(gf.GFError):
+        gf.gf_workspace_bytes([(8, 8, 8, 8)], gf.GF_LANDAU, gf.GF_FP32_12, gf.GF_FLAG_AUTOGRAD)
