@@ -1143,9 +1143,9 @@ int gf_set_sweep_variant(gf_handle* h, int variant) {
 int gf_autotune(gf_handle* h, int* threads_out, int* variant_out) {
   if (!h) return GF_EINVAL;
   // Time a few sweeps of the current field for every launch shape and keep the fastest.
-  // Half-sweeps of one parity on the same field change it, so the sweeps are done in
-  // pairs on a scratch copy: the field is saved to the staging area first when it fits,
-  // otherwise the tuning sweeps act on the field itself (they are gauge transformations).
+  // The tuning sweeps act on the field itself: they are gauge transformations (the
+  // gauge-invariant content is unchanged), but a run meant to start from the original
+  // configuration uploads it again afterwards.
   const int st = cur_storage(h);
   std::vector<std::pair<int, int>> cands;
   for (int t : {64, 128, 256}) {
@@ -1153,8 +1153,10 @@ int gf_autotune(gf_handle* h, int* threads_out, int* variant_out) {
     if (st == GF_FP32_12) cands.push_back({t, GF_SWEEP_PIPELINED});
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  GF_CK(h, cudaEventCreate(&e0));
-  GF_CK(h, cudaEventCreate(&e1));
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return fail(h, GF_ECUDA, "event creation failed");
+  }
   float best = 1e30f;
   int bt = h->threads, bv = h->variant;
   int rc = GF_OK;

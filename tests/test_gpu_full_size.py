@@ -146,3 +146,41 @@ def test_large_lattice_relaxation_never_decreases_F(gf):
         assert F >= F_prev - 2e-7 * abs(F_prev), (k, F, F_prev)
         F_prev = F
     fx.close()
+
+
+def test_autograd_32x4_gradient_and_sgd(gf):
+    # the workload's differentiable F at 32^4 (FP64 links, c zero-initialised): the
+    # gradient at c = 0 is Tr[lambda_a Delta] / (2i nd Nc V), the first SGD step with
+    # lr = alpha nd Nc V / 2 on -F is the naive steepest-descent step of Eq. (7), and 50
+    # steps never lower F
+    from paper_1412_1498_gb300.autograd import functional_theta
+    dims = (32, 32, 32, 32)
+    V = 32 ** 4
+    alpha = 0.08
+    U = fields.random_gauge_config(dims, 0.5, 5)
+    fx = gf.GaugeFixer(dims, gf.GF_LANDAU, gf.GF_FP64_18, autograd=True)
+    fx.upload(U)
+    c = torch.zeros((V, 8), dtype=torch.float64, device="cuda", requires_grad=True)
+    F0, th0 = functional_theta(c, fx)
+    rF, rth, _, _ = oracle.measure(U)
+    assert abs(F0.item() - rF) <= 1e-12 * abs(rF) and abs(th0.item() - rth) <= 1e-12 * rth
+    F0.backward()
+    D = oracle.delta(U)
+    want = (np.einsum("aij,sji->sa", fields.gell_mann(), D.reshape(V, 3, 3)) / (2j * 4 * 3 * V)).real
+    assert np.abs(c.grad.cpu().numpy() - want).max() < 1e-12 * np.abs(want).max()
+    opt = torch.optim.SGD([c], lr=alpha * 4 * 3 * V / 2)
+    Fs = []
+    for step in range(50):
+        opt.zero_grad()
+        F, th = functional_theta(c, fx)
+        Fs.append(F.item())
+        (-F).backward()
+        opt.step()
+        if step == 0:
+            W = fields.gauge_transform(U, fields.expi_hermitian(-0.5j * alpha * D.reshape(dims[::-1] + (3, 3)), 1.0))
+            F1, _ = functional_theta(c.detach(), fx)
+            assert abs(F1.item() - oracle.measure(W)[0]) < 1e-12
+    F, th = functional_theta(c.detach(), fx)
+    Fs.append(F.item())
+    assert np.all(np.diff(Fs) > -1e-13) and Fs[-1] > Fs[0] and th.item() < th0.item()
+    fx.close()
