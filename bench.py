@@ -357,32 +357,37 @@ def run_gpu(args):
         _, _, Ff, thf = gf.gf_fix(f4.h, 1e-300, args.fasd_iters)
         q1.record(stream)
         q1.synchronize()
-        fasd = {"iterations": args.fasd_iters, "ms_per_iteration": q0.elapsed_time(q1) / args.fasd_iters,
+        ms_it = q0.elapsed_time(q1) / args.fasd_iters
+        # HBM bytes an iteration must move: links read for Delta (4 V b) and read and
+        # written in the update (8 V b), g written and read once (2 x 48 V B), k-space
+        # (4 complex FP32 fields, 32 V B) written and read back once; the z/t transform
+        # works on L2-resident k-space
+        fasd_bytes = 12 * V * LINK_B + 2 * 48 * V + 2 * 32 * V
+        fasd = {"iterations": args.fasd_iters, "ms_per_iteration": ms_it,
+                "algorithmic_GBps": fasd_bytes / (ms_it * 1e-3) / 1e9, "bytes_per_iteration": fasd_bytes,
                 "theta_start": float(th0), "theta_end": float(thf[0]), "F_end": float(Ff[0]),
                 "workload": "32^4 Landau, FP32-12 links, FP32 FFTs, FP64 reductions, eps 0.5 seed 5, alpha 0.08"}
         f4.close()
         del f4, U5
 
-    # ---- differentiable F(c), theta(c): forward and backward on 16^4 FP64
+    # ---- differentiable F(c), theta(c): forward and backward on the 32^4 FP64 field
     autograd = None
     if args.autograd:
         from paper_1412_1498_gb300.autograd import functional_theta
-        d16 = (16, 16, 16, 16)
-        V16 = 16 ** 4
-        f5 = gf.GaugeFixer(d16, gf.GF_LANDAU, gf.GF_FP64_18, autograd=True, device=dev)
-        f5.upload(make_field(d16, EPS_FIELD, 5))
-        c = torch.zeros((V16, 8), dtype=torch.float64, device=dev, requires_grad=True)
+        f5 = gf.GaugeFixer(DIMS, gf.GF_LANDAU, gf.GF_FP64_18, autograd=True, device=dev)
+        f5.upload(make_field(DIMS, EPS_FIELD, 5))
+        c = torch.zeros((V, 8), dtype=torch.float64, device=dev, requires_grad=True)
         for _ in range(2):
-            F16, _t = functional_theta(c, f5)
-            F16.backward()
+            Fa, _t = functional_theta(c, f5)
+            Fa.backward()
         r0, r1, r2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         r0.record(stream)
-        F16, _t = functional_theta(c, f5)
+        Fa, _t = functional_theta(c, f5)
         r1.record(stream)
-        F16.backward()
+        Fa.backward()
         r2.record(stream)
         r2.synchronize()
-        autograd = {"lattice": list(d16), "forward_ms": r0.elapsed_time(r1), "backward_ms": r1.elapsed_time(r2)}
+        autograd = {"lattice": list(DIMS), "forward_ms": r0.elapsed_time(r1), "backward_ms": r1.elapsed_time(r2)}
         f5.close()
         del f5
 
