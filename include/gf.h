@@ -173,9 +173,13 @@ GF_API int gf_reunitarize(gf_handle *h);
 /*
  * Algorithm 1: measure; while a unit has theta >= eps and fewer than maxiter sweeps
  * were done: even half-sweep, odd half-sweep (reunitarising the links it writes after
- * every reunit_interval-th sweep), then F and theta every check_interval sweeps; a
- * unit whose theta < eps is masked and no longer updated.  The schedule counts sweeps
- * from the last upload (see gf_get_sweeps_done).
+ * every reunit_interval-th sweep), then the stop check every check_interval sweeps; a
+ * unit whose theta < eps is masked and no longer updated.  The check forms F and the
+ * odd-site part of theta inside the odd half-sweep; theta >= that part, so a unit whose
+ * odd part alone reaches eps continues exactly as the full theta would decide, and the
+ * even-site part is computed only for the other units and on the last sweep of the
+ * budget.  F, theta and the masks at exit are exact (gf_set_history records theta at
+ * every check).  The schedule counts sweeps from the last upload (gf_get_sweeps_done).
  *   eps > 0; maxiter >= 0.  iters (nullable): gf_num_units ints, sweeps each unit
  *   received.  F, theta (nullable): n_lat final values.
  *   With GF_FLAG_MIXED: FP32 sweeps until every unit has theta < the switch threshold
