@@ -83,12 +83,10 @@ __host__ __device__ constexpr int bit_rev(int r, int logL) {
   return o;
 }
 
+// decimation in frequency on registers: natural order in, bit-reversed order out
 template <class T, int LOGL>
-__device__ __forceinline__ void fft_line_reg(cx<T>* d, int estride, const cx<T>* tw, int sign) {
+__device__ __forceinline__ void dif_reg(cx<T> (&v)[1 << LOGL], const cx<T>* tw, int sign) {
   constexpr int L = 1 << LOGL;
-  cx<T> v[L];
-#pragma unroll
-  for (int k = 0; k < L; ++k) v[k] = d[k * estride];
 #pragma unroll
   for (int span = L / 2; span >= 1; span >>= 1) {
 #pragma unroll
@@ -107,8 +105,66 @@ __device__ __forceinline__ void fft_line_reg(cx<T>* d, int estride, const cx<T>*
       }
     }
   }
+}
+
+template <class T, int LOGL>
+__device__ __forceinline__ void fft_line_reg(cx<T>* d, int estride, const cx<T>* tw, int sign) {
+  constexpr int L = 1 << LOGL;
+  cx<T> v[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) v[k] = d[k * estride];
+  dif_reg<T, LOGL>(v, tw, sign);
 #pragma unroll
   for (int r = 0; r < L; ++r) d[bit_rev(r, LOGL) * estride] = v[r];
+}
+
+// decimation in time on registers: bit-reversed order in, natural order out
+template <class T, int LOGL>
+__device__ __forceinline__ void dit_reg(cx<T> (&v)[1 << LOGL], const cx<T>* tw, int sign) {
+  constexpr int L = 1 << LOGL;
+#pragma unroll
+  for (int span = 1; span < L; span <<= 1) {
+#pragma unroll
+    for (int s = 0; s < L; s += 2 * span) {
+#pragma unroll
+      for (int j = 0; j < span; ++j) {
+        const cx<T> a = v[s + j];
+        cx<T> b = v[s + j + span];
+        if (j != 0) {
+          cx<T> w = tw[j * (L / (2 * span))];  // exp(-2 pi i j / (2 span))
+          if (sign > 0) w.im = -w.im;
+          b = cmul(b, w);
+        }
+        v[s + j] = cadd(a, b);
+        v[s + j + span] = csub(a, b);
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ float filter_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double filter_div(double a, double b) { return a / b; }
+
+// The last transform direction of a line, the Fourier filter and the inverse in one
+// pass: forward transform by decimation in frequency (modes in bit-reversed order), each
+// mode k scaled in place by coef / (base + s2[k]) (0 where that is not positive: the
+// zero mode), inverse transform by decimation in time (bit-reversed in, natural out).
+template <class T, int LOGL>
+__device__ __forceinline__ void filter_line_reg(cx<T>* d, int estride, const cx<T>* tw, T base,
+                                                const T* s2, T coef) {
+  constexpr int L = 1 << LOGL;
+  cx<T> v[L];
+#pragma unroll
+  for (int k = 0; k < L; ++k) v[k] = d[k * estride];
+  dif_reg<T, LOGL>(v, tw, -1);
+#pragma unroll
+  for (int r = 0; r < L; ++r) {
+    const T p2 = base + s2[bit_rev(r, LOGL)];
+    v[r] = cscale(v[r], p2 > T(0) ? filter_div(coef, p2) : T(0));
+  }
+  dit_reg<T, LOGL>(v, tw, +1);
+#pragma unroll
+  for (int k = 0; k < L; ++k) d[k * estride] = v[k];
 }
 
 template <class T>
@@ -387,7 +443,7 @@ __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
 // col[kxl + KX z + (KX Lz + KX) tl]: the pad keeps both transform directions free of bank
 // conflicts.
 template <class T, int ND>
-__global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
+__global__ void __launch_bounds__(256, 2) k_fasd_zt(FasdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ cx<T> twz[32], twt[32];
   __shared__ T s2z[64], s2t[64];   // 4 sin^2(pi k / L) along z and t
@@ -413,11 +469,10 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
       const T sn = sinpi((T)k / (T)Lt);
       s2t[k] = T(4) * sn * sn;
     }
-  T p2xy[8];
-#pragma unroll
-  for (int j = 0; j < 8; ++j) {
-    const T sx = sinpi((T)(kx0 + (j < KX ? j : 0)) / (T)Lx), sy = sinpi((T)ky / (T)Ly);
-    p2xy[j] = T(4) * sx * sx + T(4) * sy * sy;
+  __shared__ T p2xy[8];  // 4 sin^2 along x + along y for the block's kx columns
+  if ((int)threadIdx.x < KX) {
+    const T sx = sinpi((T)(kx0 + (int)threadIdx.x) / (T)Lx), sy = sinpi((T)ky / (T)Ly);
+    p2xy[threadIdx.x] = T(4) * sx * sx + T(4) * sy * sy;
   }
   __syncthreads();
   cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf) + f * lat.V;
@@ -430,19 +485,52 @@ __global__ void __launch_bounds__(256) k_fasd_zt(FasdArgs a) {
     col[kxl + KX * z + pitch * tl] = kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl];
   }
   __syncthreads();
-  fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);          // along z
-  if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, -1);  // along t
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int kxl = i & mk, kz = (i >> lk) & mz, kt = i >> (lk + lz);
-    T p2 = p2xy[kxl] + s2z[kz];
-    if (ND == 4) p2 += s2t[kt];
-    const T fac = p2 > T(0) ? (T)a.coef / p2 : T(0);
-    const int c = kxl + KX * kz + pitch * kt;
-    col[c] = cscale(col[c], fac);
+  const int lf = ND == 4 ? a.logL[3] : lz;  // the direction transformed last
+  if (lf <= 5 && lz <= 5) {
+    // lines through registers; the last direction is transformed, filtered and
+    // transformed back in one pass (filter_line_reg)
+    const T coef = (T)a.coef;
+    if (ND == 4) {
+      fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);  // along z
+      for (int l = threadIdx.x; l < Lz * KX; l += blockDim.x) {     // along t: line (kxl, kz)
+        const T base = p2xy[l & mk] + s2z[l >> lk];
+        switch (lf) {
+          case 1: filter_line_reg<T, 1>(col + l, pitch, twt, base, s2t, coef); break;
+          case 2: filter_line_reg<T, 2>(col + l, pitch, twt, base, s2t, coef); break;
+          case 3: filter_line_reg<T, 3>(col + l, pitch, twt, base, s2t, coef); break;
+          case 4: filter_line_reg<T, 4>(col + l, pitch, twt, base, s2t, coef); break;
+          default: filter_line_reg<T, 5>(col + l, pitch, twt, base, s2t, coef); break;
+        }
+      }
+      __syncthreads();
+      fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
+    } else {
+      for (int l = threadIdx.x; l < KX; l += blockDim.x) {  // along z: line kxl of the slice
+        switch (lf) {
+          case 1: filter_line_reg<T, 1>(col + l, KX, twz, p2xy[l], s2z, coef); break;
+          case 2: filter_line_reg<T, 2>(col + l, KX, twz, p2xy[l], s2z, coef); break;
+          case 3: filter_line_reg<T, 3>(col + l, KX, twz, p2xy[l], s2z, coef); break;
+          case 4: filter_line_reg<T, 4>(col + l, KX, twz, p2xy[l], s2z, coef); break;
+          default: filter_line_reg<T, 5>(col + l, KX, twz, p2xy[l], s2z, coef); break;
+        }
+      }
+      __syncthreads();
+    }
+  } else {
+    fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);          // along z
+    if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, -1);  // along t
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int kxl = i & mk, kz = (i >> lk) & mz, kt = i >> (lk + lz);
+      T p2 = p2xy[kxl] + s2z[kz];
+      if (ND == 4) p2 += s2t[kt];
+      const T fac = p2 > T(0) ? (T)a.coef / p2 : T(0);
+      const int c = kxl + KX * kz + pitch * kt;
+      col[c] = cscale(col[c], fac);
+    }
+    __syncthreads();
+    if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, +1);
+    fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
   }
-  __syncthreads();
-  if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, +1);
-  fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
 #pragma unroll 8
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);

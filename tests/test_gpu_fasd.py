@@ -24,7 +24,8 @@ def gf():
     return m
 
 
-@pytest.mark.parametrize("gauge,dims", [(0, (8, 8, 8, 8)), (0, (8, 4, 16, 2)), (1, (8, 8, 4, 6)), (1, (4, 16, 8, 2))])
+@pytest.mark.parametrize("gauge,dims", [(0, (8, 8, 8, 8)), (0, (8, 4, 16, 2)), (1, (8, 8, 4, 6)), (1, (4, 16, 8, 2)),
+                                        (0, (4, 2, 4, 64)), (0, (2, 4, 64, 4)), (1, (2, 4, 64, 2))])
 @pytest.mark.parametrize("storage", [0, 2])
 def test_one_step_against_oracle(gf, gauge, dims, storage):
     U = fields.random_gauge_config(dims, 0.5, 95)
