@@ -88,10 +88,12 @@ __device__ __forceinline__ void su2_left_mul(cx<T> (&M)[9], int i, int j, cx<T> 
 
 // G = product of the three subgroup maximisers for K (Cabibbo-Marinari order (0,1),
 // (0,2), (1,2)), K rotated after each one.
-// The first product R1 * 1 is R1 itself and K is not needed after the third step; both
-// shortcuts give the values of the plain sequence (x * 1 = x, x + 0 = x).
+// The first product R1 * 1 is R1 itself (x * 1 = x, x + 0 = x: the values of the plain
+// sequence).  K is left as R2 R1 K unless rotate_last asks for the third rotation too,
+// which leaves K = G K (used by the fused check, see site_check_from_GK).
 template <class T, bool REPRO, int FORM>
-__device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega) {
+__device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega,
+                                           bool rotate_last = false) {
   cx<T> a, b;
   su2_maximiser<T, REPRO, FORM>(K, 0, 1, omega, a, b);
   su2_left_mul(K, 0, 1, a, b);
@@ -107,6 +109,7 @@ __device__ __forceinline__ void su3_update(cx<T> (&K)[9], cx<T> (&G)[9], T omega
   su2_left_mul(G, 0, 2, a, b);
   su2_maximiser<T, REPRO, FORM>(K, 1, 2, omega, a, b);
   su2_left_mul(G, 1, 2, a, b);
+  if (rotate_last) su2_left_mul(K, 1, 2, a, b);
 }
 
 // K += U_mu(x) + U_mu(x - mu)^dagger (in-place form of Eq. (5))
@@ -160,6 +163,19 @@ __device__ __forceinline__ T theta_site(const cx<T> (&A)[9]) {
 #pragma unroll
   for (int e = 0; e < 9; ++e) q = q + (D[e].re * D[e].re + D[e].im * D[e].im);
   return q;
+}
+
+// F and Tr[Delta Delta^dagger] of a site just updated, from K' = G K (K of Eq. (5) before
+// the update).  The site's new links are G U_mu(x) and U_mu(x - mu) G^dagger, so
+// K' = sum_mu [U'_mu(x) + U'_mu(x - mu)^dagger]; then A' = sum_mu [U'_mu(x - mu) - U'_mu(x)]
+// of Eq. (3) has A' - A'^dagger = K'^dagger - K', so Delta(x) is the traceless
+// anti-Hermitian part of K' up to its sign, and Re Tr K' is the site's share of Eq. (1)
+// (each of its links counted once).  The values are those of the links before any
+// reunitarisation of the same sweep.
+template <class T>
+__device__ __forceinline__ void site_check_from_GK(const cx<T> (&Kp)[9], T& fs, T& q) {
+  fs = (Kp[0].re + Kp[4].re) + Kp[8].re;
+  q = theta_site(Kp);
 }
 
 // Per-tile partial sums: FP64 storage reduces in FP64; FP32 storage in compensated FP32
@@ -351,6 +367,8 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
     cx<T> K[9], G[9];
 #pragma unroll
     for (int e = 0; e < 9; ++e) K[e] = {T(0), T(0)};
+    // FP32 sweeps take the check from G K; FP64 ones sum the stored links' A (Eq. (3))
+    constexpr bool kCheckGK = sizeof(T) == 4;
 
     if constexpr (KEEP) {
       cx<T> f[4][NE], b[4][NE];
@@ -361,7 +379,8 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
       }
 #pragma unroll
       for (int mu = 0; mu < ND; ++mu) add_to_K(K, f[mu], b[mu]);
-      su3_update<T, REPRO, FORM>(K, G, omega);
+      su3_update<T, REPRO, FORM>(K, G, omega, kCheckGK && measure_now);
+      if (kCheckGK && measure_now) site_check_from_GK(K, fs, q);
       cx<T> A[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
@@ -373,11 +392,11 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
           reunit(f[mu]);
           reunit(b[mu]);
         }
-        if (mu < ND && measure_now) add_to_A_F(A, fs, f[mu], b[mu]);
+        if (!kCheckGK && mu < ND && measure_now) add_to_A_F(A, fs, f[mu], b[mu]);
         St::store(base, V, mu, idx_f, f[mu]);
         St::store(base, V, mu, idx_b[mu], b[mu]);
       }
-      if (measure_now) q = theta_site(A);
+      if (!kCheckGK && measure_now) q = theta_site(A);
     } else {
 #pragma unroll
       for (int mu = 0; mu < ND; ++mu) {
@@ -386,7 +405,8 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
         St::load(base, V, mu, idx_b[mu], b);
         add_to_K(K, f, b);
       }
-      su3_update<T, REPRO, FORM>(K, G, omega);
+      su3_update<T, REPRO, FORM>(K, G, omega, kCheckGK && measure_now);
+      if (kCheckGK && measure_now) site_check_from_GK(K, fs, q);
       cx<T> A[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) A[e] = {T(0), T(0)};
@@ -401,11 +421,11 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
           reunit(f);
           reunit(b);
         }
-        if (mu < ND && measure_now) add_to_A_F(A, fs, f, b);
+        if (!kCheckGK && mu < ND && measure_now) add_to_A_F(A, fs, f, b);
         St::store(base, V, mu, idx_f, f);
         St::store(base, V, mu, idx_b[mu], b);
       }
-      if (measure_now) q = theta_site(A);
+      if (!kCheckGK && measure_now) q = theta_site(A);
     }
   }
   if (measure_now) {

@@ -114,10 +114,8 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
           pipe_read(slot, B, 12 + 3 * mu, b);
           add_to_K(K, f, b);
         }
-        su3_update<float, false, FORM>(K, G, omega);
-        cx<float> A[9];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) A[e] = {0.f, 0.f};
+        su3_update<float, false, FORM>(K, G, omega, measure_now);
+        if (measure_now) site_check_from_GK(K, fs, q);
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
           cx<float> f[6], b[6];
@@ -129,7 +127,6 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
             reunit(f);
             reunit(b);
           }
-          if (mu < ND && measure_now) add_to_A_F(A, fs, f, b);
 #pragma unroll
           for (int w = 0; w < 3; ++w) {
             g[(long long)(w * 4 + mu) * lat.V + cur.idx_f] =
@@ -138,7 +135,6 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
                 make_float4(b[2 * w].re, b[2 * w].im, b[2 * w + 1].re, b[2 * w + 1].im);
           }
         }
-        if (measure_now) q = theta_site(A);
       }
       if (measure_now) {
         const float v[2] = {fs, q};

@@ -292,6 +292,45 @@ def check_subgroup_fixed_point_after_site_update(orc, gauge):
         assert abs(a - 1) < 1e-12 and abs(bb) < 1e-12, (site, a, bb)
 
 
+def check_updated_site_delta_from_GK(orc, gauge):
+    # The identity behind the fused check of the FP32 sweeps: after a site's update by G,
+    # Delta(x) of Eq. (3) is the traceless anti-Hermitian part of G K (K of Eq. (5) from
+    # the links before the update) with the sign of K'^dagger - K', and Re Tr G K is the
+    # site's share of the Eq. (1) sum.  Pinned on every odd site of a half-sweep, with G
+    # read off the updated links and Delta, F from the oracle's own Eqs. (1), (3).
+    nd = 4 if gauge == orc.LANDAU else 3
+    dims = (4, 4, 6, 4)
+    U = fields.random_gauge_config(dims, 0.5, 19)
+    W = orc.or_half_sweep(U.copy(), 1, 1.7, gauge)
+    D = orc.delta(W, gauge)
+    Lt, Lz, Ly, Lx = U.shape[:4]
+    fsum = 0.0
+    n_odd = 0
+    for site in np.ndindex(Lt, Lz, Ly, Lx):
+        if sum(site) % 2 == 0:
+            continue
+        n_odd += 1
+        G = W[site][0] @ U[site][0].conj().T
+        K = np.zeros((3, 3), complex)
+        for mu in range(4):
+            b = list(site)
+            ax = obs.AXIS[mu]
+            b[ax] = (b[ax] - 1) % U.shape[ax]
+            b = tuple(b)
+            assert np.abs(W[site][mu] - G @ U[site][mu]).max() < 1e-13
+            assert np.abs(W[b][mu] - U[b][mu] @ G.conj().T).max() < 1e-13
+            if mu < nd:
+                K += U[site][mu] + U[b][mu].conj().T
+        Kp = G @ K
+        A = Kp.conj().T - Kp
+        A -= np.trace(A) / 3 * np.eye(3)
+        assert np.abs(D[site] - A).max() < 1e-13, site
+        fsum += np.trace(Kp).real
+    F, _, _, _ = orc.measure(W, gauge)
+    assert abs(fsum / (nd * 3 * U[..., 0, 0, 0].size) - F) < 1e-14
+    assert n_odd == U[..., 0, 0, 0].size // 2
+
+
 def check_even_translation_covariance_is_exact(orc):
     U = fields.random_gauge_config((4, 4, 4, 6), 0.5, 15)
     W = np.roll(U, shift=(2, 1, 1), axis=(0, 1, 3)).copy()   # shift by t+2, z+1, x+1: even

@@ -27,6 +27,8 @@ CASES = [
     (C.check_half_sweep_touches_only_its_parity, ()),
     (C.check_subgroup_fixed_point_after_site_update, (L,)),
     (C.check_subgroup_fixed_point_after_site_update, (CO,)),
+    (C.check_updated_site_delta_from_GK, (L,)),
+    (C.check_updated_site_delta_from_GK, (CO,)),
     (C.check_even_translation_covariance_is_exact, ()),
     (C.check_reunit_is_gram_schmidt_projection, ()),
     (C.check_fix_stop_rule_and_bookkeeping, ()),
