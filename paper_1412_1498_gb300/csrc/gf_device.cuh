@@ -542,6 +542,7 @@ __device__ __forceinline__ void block_sum_f32(const float (&v)[NV], double (&out
       float l = lane < nw ? smem[(2 * k + 1) * 32 + lane] : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
+        if (o >= nw) continue;  // lanes >= nw hold zeros: those levels add exact zeros
         const float oh = __shfl_down_sync(0xffffffffu, h, o);
         const float ol = __shfl_down_sync(0xffffffffu, l, o);
         float s, e;
@@ -590,6 +591,7 @@ __device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float2 (&out
       float l = lane < nw ? smem[(2 * k + 1) * 32 + lane] : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
+        if (o >= nw) continue;  // lanes >= nw hold zeros: those levels add exact zeros
         const float oh = __shfl_down_sync(0xffffffffu, h, o);
         const float ol = __shfl_down_sync(0xffffffffu, l, o);
         float s, e;

@@ -78,7 +78,8 @@ __device__ __forceinline__ void pipe_read(const float4* slot, int B, int word0, 
 template <int ND, int FORM>
 __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
   extern __shared__ float4 sm[];
-  __shared__ double red[64];
+  __shared__ double red[2][64];  // alternate per tile sum: no barrier after the sum
+  int rb = 0;
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
     if (!state_running(a.st)) return;
@@ -139,12 +140,14 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
       if (measure_now) {
         const float v[2] = {fs, q};
         float2 o[2];
-        block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
+        block_sum_f32<2>(v, o, reinterpret_cast<float*>(red[rb]));
         if (threadIdx.x == 0) {
           if (a.part_F) a.part_F[cur.ti] = o[0];
           a.part_theta[cur.ti] = o[1];
         }
-        __syncthreads();  // red[] is reused by the next tile
+        // red[rb] is written again two sums later, after the next sum's barrier, which
+        // warp 0 reaches only once it has read this one
+        rb ^= 1;
       }
     }
     if (kn >= a.n_tiles) break;
@@ -198,7 +201,8 @@ __device__ __forceinline__ MeasSite meas_issue(const MeasureArgs& a, int k, int 
 template <int ND>
 __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
   extern __shared__ float4 sm[];
-  __shared__ double red[64];
+  __shared__ double red[2][64];  // alternate per tile sum, as in k_or_sweep_pipe
+  int rb = 0;
   if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
   int k = blockIdx.x;
   if (k >= a.n_tiles) return;
@@ -235,12 +239,12 @@ __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
       }
       const float v[2] = {fsum, q};
       float2 o[2];
-      block_sum_f32<2>(v, o, reinterpret_cast<float*>(red));
+      block_sum_f32<2>(v, o, reinterpret_cast<float*>(red[rb]));
       if (threadIdx.x == 0) {
         if (a.part_F) a.part_F[cur.ti] = o[0];
         a.part_theta[cur.ti] = o[1];
       }
-      __syncthreads();  // red[] is reused by the next tile
+      rb ^= 1;
     }
     if (kn >= a.n_tiles) break;
     k = kn;
