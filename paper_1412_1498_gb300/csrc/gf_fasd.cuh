@@ -234,15 +234,18 @@ __device__ __forceinline__ void g_load(const char* gbuf, long long V, int idx, c
 #pragma unroll
     for (int w = 0; w < 3; ++w) {
       const float4 v = p[w * V + idx];
-      g[2 * w] = {v.x, v.y};
-      g[2 * w + 1] = {v.z, v.w};
+      g[2 * w].re = v.x;
+      g[2 * w].im = v.y;
+      g[2 * w + 1].re = v.z;
+      g[2 * w + 1].im = v.w;
     }
   } else {
     const double2* p = reinterpret_cast<const double2*>(gbuf);
 #pragma unroll
     for (int w = 0; w < 6; ++w) {
       const double2 v = p[w * V + idx];
-      g[w] = {v.x, v.y};
+      g[w].re = v.x;
+      g[w].im = v.y;
     }
   }
   third_row(g, g + 6);
