@@ -31,7 +31,7 @@
  *    (a' = 1 - omega + omega*a, b' = omega*b, renormalised) or exactly.
  *  - Coulomb gauge: the temporal links are transformed with the spatial ones
  *    (Algorithm 1 applies g(x) "for all mu") but enter neither K nor F nor Delta.
- *  - reunitarisation (Section 3: "at each 20 steps") projects each link back to SU(3)
+ *  - reunitarisation (Section 3: every 20 steps) projects each link back to SU(3)
  *    by Gram-Schmidt on rows 0 and 1, row 2 = conj(row0 x row1); it is applied to the
  *    links the odd half-sweep has just written, which is every link when all sites
  *    are active.
