@@ -1,4 +1,4 @@
-"""The benchmark's multi-rank bookkeeping on CPU (gloo, world size 2): each rank fixes its
+"""The benchmark's multi-rank bookkeeping on CPU (gloo, world size 2): each rank times its
 own lattice (weak scaling, no data-path collective); the job's time is the slowest
 rank's and the throughput counts the work of every rank."""
 import os
@@ -32,7 +32,7 @@ def _worker(rank, world, port, out):
 def test_reduce_over_ranks_two_ranks():
     world = 2
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:   # no fork of this threaded process
         out = m.dict()
         mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
