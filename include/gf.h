@@ -179,7 +179,12 @@ GF_API int gf_reunitarize(gf_handle *h);
  * odd part alone reaches eps continues exactly as the full theta would decide, and the
  * even-site part is computed only for the other units and on the last sweep of the
  * budget.  F, theta and the masks at exit are exact (gf_set_history records theta at
- * every check).  The schedule counts sweeps from the last upload (gf_get_sweeps_done).
+ * every check).  FP32 storages take the odd-site values from K' = G K (K of Eq. (5)
+ * before the site's update, G its new transformation: Delta of the updated links is the
+ * traceless anti-Hermitian part of K', Re Tr K' the site's share of Eq. (1)), i.e. of the
+ * links before a reunitarisation in the same sweep, a difference at the rounding level;
+ * FP64 and the double-float polish sum the stored links.  The schedule counts sweeps
+ * from the last upload (gf_get_sweeps_done).
  *   eps > 0; maxiter >= 0.  iters (nullable): gf_num_units ints, sweeps each unit
  *   received.  F, theta (nullable): n_lat final values.
  *   With GF_FLAG_MIXED: FP32 sweeps until every unit has theta < the switch threshold
