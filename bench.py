@@ -204,6 +204,60 @@ def run_reference(args):
     }))
 
 
+def units_probe(gf, dev, stream, n_coulomb: int = 400, n_ensemble: int = 200):
+    """Throughput of the batched-unit workloads (FP32-12 sweeps with the stop check after
+    every sweep, eps = 1e-300 so every unit stays active, autotuned launch shape): the
+    Coulomb 32^3 x 64 field (eps 0.5, seed 4) with its 64 time slices as units, and the
+    48-lattice ensemble (16 x 16^4, 16 x 24^4, 16 x 16^3 x 32; eps ~ U[0.3, 0.6], seeds
+    100-147) in one batch.  Link bytes are counted as 16 V b per sweep."""
+    import torch
+    from paper_1412_1498_gb300 import fields
+
+    def timed(h, n):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        gf.gf_fix(h, 1e-300, n)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / n
+
+    out = {}
+    dims = (32, 32, 32, 64)
+    U = make_field(dims, EPS_FIELD, 4)
+    fx = gf.GaugeFixer(dims, gf.GF_COULOMB, gf.GF_FP32_12, device=dev)
+    fx.upload(U)
+    gf.gf_autotune(fx.h)
+    fx.upload(U)
+    gf.gf_fix(fx.h, 1e-300, 5)                    # graph capture
+    fx.upload(U)
+    ms = timed(fx.h, n_coulomb)
+    vol = 32 * 32 * 32 * 64
+    out["coulomb_32x32x32x64"] = {"sweeps": n_coulomb, "ms_per_sweep": ms, "slice_sweeps_per_s": 64e3 / ms,
+                                  "link_GBps": 16 * vol * LINK_B / (ms * 1e-3) / 1e9}
+    fx.close()
+    del fx, U
+    dims_list = [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 24)] * 16 + [(16, 16, 16, 32)] * 16
+    Us = fields.ensemble(dims_list, list(range(100, 148)))
+    fb = gf.GaugeFixer(dims_list, gf.GF_LANDAU, gf.GF_FP32_12, device=dev)
+
+    def upload_all():
+        for i, Ui in enumerate(Us):
+            fb.upload(Ui, i)
+
+    upload_all()
+    gf.gf_autotune(fb.h)
+    upload_all()
+    gf.gf_fix(fb.h, 1e-300, 5)
+    upload_all()
+    ms = timed(fb.h, n_ensemble)
+    vtot = sum(d[0] * d[1] * d[2] * d[3] for d in dims_list)
+    out["ensemble_48"] = {"sweeps": n_ensemble, "ms_per_sweep": ms, "unit_sweeps_per_s": 48e3 / ms,
+                          "site_updates_per_s": vtot * 1e3 / ms,
+                          "link_GBps": 16 * vtot * LINK_B / (ms * 1e-3) / 1e9}
+    fb.close()
+    return out
+
+
 # ------------------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -391,6 +445,9 @@ def run_gpu(args):
         f5.close()
         del f5
 
+    # ---- batched units: Coulomb time slices, the 48-lattice ensemble (opt-in)
+    units = units_probe(gf, dev, stream) if args.units_probe else None
+
     peak, peak_kind = measured_peaks()
     achieved = HALF_SWEEP_BYTES / (half_ms * 1e-3) / 1e9
     traffic = None
@@ -438,6 +495,7 @@ def run_gpu(args):
             "split_polish_probe": split_probe,
             "fa_sd": fasd,
             "autograd": autograd,
+            "units_probe": units,
         }
         print(json.dumps(line))
     fx.close()
@@ -459,6 +517,8 @@ def main():
     # 63 iterations and the final measurement fill four 16-iteration graph replays exactly
     ap.add_argument("--fasd-iters", type=int, default=63)
     ap.add_argument("--autograd", type=int, default=1)
+    ap.add_argument("--units-probe", action="store_true",
+                    help="also time the Coulomb 32^3x64 slices and the 48-lattice ensemble")
     ap.add_argument("--launch", default="", help="fixed launch shape THREADS:register|pipelined "
                     "instead of the autotuner (for profiler runs)")
     args = ap.parse_args()
