@@ -18,7 +18,7 @@
  *    s = x + Lx*(y + Ly*(z + Lz*t)) starts at element 2*9*(4*s + mu).
  *  - Site parity p(x) = (x + y + z + t) mod 2; parity 0 ("even") is updated first.
  *  - Landau gauge uses nd = 4 directions in K(x), F and Delta(x); Coulomb gauge uses
- *    nd = 3 (the temporal links are still transformed, Algorithm 1 "for all mu").
+ *    nd = 3 (the temporal links are still transformed: Algorithm 1 updates every mu).
  *    F is normalised by 1/(nd * 3 * V) so that the unit field has F = 1.
  *  - A handle holds one lattice (gf_create) or a batch of independent lattices
  *    (gf_create_batch).  Convergence units: one per lattice for Landau gauge, one per
@@ -92,7 +92,8 @@ typedef struct gf_handle gf_handle;
  * Bytes of device workspace a handle needs.
  *   n_lat: number of lattices (1 for gf_create); dims: n_lat * 4 ints as above;
  *   gauge: GF_LANDAU | GF_COULOMB; storage: one of the GF_FP* codes above;
- *   flags: 0 or a combination of GF_FLAG_* (GF_FLAG_MIXED for the FP32 storages).  *bytes receives the size.  Returns GF_EINVAL on bad
+ *   flags: 0 or a combination of GF_FLAG_* (GF_FLAG_MIXED for the FP32 storages).
+ *   *bytes receives the size.  Host-only (no CUDA call).  Returns GF_EINVAL on bad
  *   arguments.
  */
 GF_API int gf_workspace_bytes(int n_lat, const int *dims, int gauge, int storage, int flags,
@@ -141,8 +142,9 @@ GF_API int gf_num_units(const gf_handle *h);
  *   elements (rows 0, 1 of 8-real storage in the storage's precision, row 2 in FP64).
  *   In mixed mode gf_fix leaves the field in the FP64 copy and download reads that copy;
  *   an upload moves the handle back to its primary storage, so upload every lattice of
- *   a batch before the next gf_fix.  Device buffers must be 16-byte aligned.  Both calls synchronise
- *   the stream when on_device = 0 (the host buffer is complete on return).
+ *   a batch before the next gf_fix.  Device buffers must be 16-byte aligned.  Both
+ *   calls synchronise the stream when on_device = 0 (the host buffer is complete on
+ *   return).
  */
 GF_API int gf_upload(gf_handle *h, int lat, const double *links, int on_device);
 GF_API int gf_download(gf_handle *h, int lat, double *links, int on_device);
