@@ -3,7 +3,7 @@
 // One iteration on one lattice:
 //   A  k_fasd_delta_xy   per (z,t) plane: Delta(x) of Eq. (3) (the argument of Eq. (8)),
 //                        F / theta partials of the current field, forward FFT along x, y;
-//   B  k_fasd_finish     per unit: F, theta, stop rule (Algorithm 2 "calculate ... theta");
+//   B  k_fasd_finish     per unit: F, theta, stop rule (the measurement step of Algorithm 2);
 //   C  k_fasd_zt         per (kx, ky): forward FFT along z (and t for Landau), the filter
 //                        (alpha/2) p^2_max / p^2 / N (k = 0 mode set to 0), inverse FFT;
 //   D  k_fasd_xy_inv_g   per (z,t) plane: inverse FFT along y, x, then
