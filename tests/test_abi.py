@@ -88,3 +88,35 @@ def test_creation_limits():
     # the differentiable functional: one FP64-18 lattice
     with pytest.raises(gf.GFError):
         gf.gf_workspace_bytes([(8, 8, 8, 8)], gf.GF_LANDAU, gf.GF_FP32_12, gf.GF_FLAG_AUTOGRAD)
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    # the boundary is a C ABI: the header compiles as strict C99, every declared entry
+    # point links from a C program, and a host-only call runs without a GPU
+    import os
+    import shutil
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = gf.header_symbols()
+    src = tmp_path / "abi.c"
+    src.write_text(
+        "#include \"gf.h\"\n#include <stdio.h>\n"
+        "typedef void (*fp)(void);\n"
+        "static const fp entry[] = {\n" + ",\n".join(f"  (fp){n}" for n in names) + "\n};\n"
+        "int main(void) {\n"
+        "  size_t bytes = 0;\n  int dims[4] = {8, 8, 8, 8};\n"
+        "  int rc = gf_workspace_bytes(1, dims, GF_LANDAU, GF_FP32_12, 0, &bytes);\n"
+        "  printf(\"%d %zu %d\\n\", rc, bytes, (int)(sizeof entry / sizeof entry[0]));\n"
+        "  return rc == GF_OK && bytes > 0 ? 0 : 1;\n}\n")
+    libdir = os.path.dirname(gf.LIB_PATH)
+    inc = os.path.dirname(gf.HEADER)
+    exe = tmp_path / "abi"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        f"-I{inc}", str(src), f"-L{libdir}", "-lgf", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, out.stderr
+    rc, nbytes, n = out.stdout.split()
+    assert rc == "0" and int(nbytes) > 0 and int(n) == len(names)
