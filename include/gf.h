@@ -122,8 +122,8 @@ GF_API int gf_create_batch(int n_lat, const int *dims, int gauge, int storage, i
 GF_API void gf_destroy(gf_handle *h);
 
 /* Message of the last failure on this handle ("" if none); h == NULL gives the message of
-   the last failed gf_create / gf_create_batch / gf_functional_theta_noalloc on this
-   thread.  Valid until the next call. */
+   the last failed gf_workspace_bytes / gf_create / gf_create_batch /
+   gf_functional_theta_noalloc on this thread.  Valid until the next call. */
 GF_API const char *gf_last_error(const gf_handle *h);
 
 /* Number of lattices and of convergence units (see conventions). */

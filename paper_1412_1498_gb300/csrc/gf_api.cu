@@ -655,9 +655,16 @@ extern "C" {
 
 int gf_workspace_bytes(int n_lat, const int* dims, int gauge, int storage, int flags, size_t* bytes) {
   std::string why;
-  if (!bytes) return GF_EINVAL;
+  g_create_error.clear();
+  if (!bytes) {
+    g_create_error = "bytes must not be NULL";
+    return GF_EINVAL;
+  }
   int rc = check_common(n_lat, dims, gauge, storage, flags, &why);
-  if (rc != GF_OK) return rc;
+  if (rc != GF_OK) {
+    g_create_error = why;
+    return rc;
+  }
   Layout L;
   plan(n_lat, dims, gauge, storage, flags, &L);
   *bytes = L.total;
