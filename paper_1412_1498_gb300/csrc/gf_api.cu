@@ -245,9 +245,15 @@ int check_common(int n_lat, const int* dims, int gauge, int storage, int flags, 
   for (int l = 0; l < n_lat; ++l) {
     const int* d = dims + 4 * l;
     if (!valid_dims(d)) {
-      char buf[160];
-      snprintf(buf, sizeof buf, "lattice %d: every extent must be even and >= 2 (got %d %d %d %d)", l,
-               d[0], d[1], d[2], d[3]);
+      char buf[200];
+      bool even = true;
+      for (int k = 0; k < 4; ++k) even = even && d[k] >= 2 && d[k] % 2 == 0;
+      if (even)
+        snprintf(buf, sizeof buf, "lattice %d: %d x %d x %d x %d sites; fewer than 2^31 are supported", l,
+                 d[0], d[1], d[2], d[3]);
+      else
+        snprintf(buf, sizeof buf, "lattice %d: every extent must be even and >= 2 (got %d %d %d %d)", l,
+                 d[0], d[1], d[2], d[3]);
       *why = buf;
       return GF_EINVAL;
     }

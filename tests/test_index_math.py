@@ -50,3 +50,13 @@ def test_limit_is_where_the_bound_stops_holding():
     bad = [n for n in range((1 << 32) // (L - 1), (1 << 32) - 1, 997 * L + L - 1)
            if (n * m) >> 32 != n // L]
     assert bad, "expected a dividend past the bound where the reciprocal is off by one"
+
+
+def test_volume_limit_message():
+    # half-volumes and plane indices are 32-bit: fewer than 2^31 sites per lattice
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_workspace_bytes([(2, 2, 2, 1 << 28)], gf.GF_LANDAU, gf.GF_FP32_12)
+    assert e.value.code == gf.GF_EINVAL and "2^31" in str(e.value)
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_workspace_bytes([(3, 2, 2, 2)], gf.GF_LANDAU, gf.GF_FP32_12)
+    assert "even" in str(e.value)
