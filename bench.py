@@ -3,17 +3,22 @@
 One step = one pass of the whole hot path over the lattice: the even and the odd
 half-sweep of Algorithm 1 (K(x), the three SU(2)-subgroup maximisers with omega = 1.7,
 g(x) applied to the 8 links; links reunitarised after every 20th sweep inside the odd
-half-sweep) followed by the F / theta reduction of Eqs. (1)-(3) (odd-site theta fused
-into the odd half-sweep, one even-site pass, one finishing reduction), on FP32 links
-stored as 12 reals.  Metric: effective link bandwidth, algorithmic link bytes of a step
-(16 V b for the sweep + 4 V b for the theta pass, b = 48 B) over the step time.
+half-sweep) and the stop check of Eqs. (1)-(3) after every sweep (F and the odd-site
+theta fused into the odd half-sweep, the finishing reduction, and the even-site theta
+pass wherever the odd part alone cannot decide the stop: on the last sweep of the
+budget here), on FP32 links stored as 12 reals, timed through gf_fix (CUDA-graph
+replay).  Metric: effective link bandwidth, the algorithmic link bytes of the run
+(16 V b per sweep, b = 48 B, plus 4 V b once for the exact check) over its time.
 
-Also reported: the roofline of the half-sweep kernel (bytes 8 V b per launch over its
-CUDA-event duration, against the measured HBM copy bandwidth), the same metric end to
-end through the C ABI with host buffers, time to theta < 1e-15 for mixed FP32->FP64
-versus pure FP64 fixing, and the CPU oracle timed on the host cores.
+Also reported: the roofline of the half-sweep kernel (8 V b per launch over its
+CUDA-event duration, against the measured HBM copy bandwidth, with ncu's DRAM bytes per
+launch when the profiled source is unchanged), the same metric end to end through the
+C ABI with pinned host buffers, time to theta < 1e-15 for pure FP64 and for mixed
+FP32 -> FP64 and FP32 -> double-float -> FP64 fixing, the double-float polish sweep,
+Fourier-accelerated steepest descent, the differentiable F/theta, optionally the
+batched Coulomb-slice and ensemble workloads, and the CPU oracle on the host cores.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--units-probe]
 """
 from __future__ import annotations
 
