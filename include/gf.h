@@ -324,7 +324,11 @@ GF_API int gf_history_count(const gf_handle *h, int *n);
  * overlap on the GPU (different streams or host threads) race on it and give wrong
  * results; calls on one stream are safe.  The first call on each device looks up the
  * array's device address with that device current, so make that first call before any
- * stream capture.  Errors: GF_EINVAL / GF_ECUDA, message in gf_last_error(NULL).
+ * stream capture.  The address is kept for the life of the process: a device reset
+ * (cudaDeviceReset, or the primary context torn down and created again) between calls
+ * is not supported.  The extents are checked before any CUDA call, with an overflow-free
+ * volume, so no input reaches the kernel with more sites than the array covers.
+ * Errors: GF_EINVAL / GF_ECUDA, message in gf_last_error(NULL).
  */
 #define GF_NOALLOC_MAX_BLOCKS 262144
 GF_API int gf_functional_theta_noalloc(const int dims[4], int gauge, const double *links,

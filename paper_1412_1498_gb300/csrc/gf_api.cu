@@ -132,8 +132,8 @@ struct Layout {
 bool valid_dims(const int* d) {
   for (int k = 0; k < 4; ++k)
     if (d[k] < 2 || (d[k] % 2) != 0) return false;
-  long long V = (long long)d[0] * d[1] * d[2] * d[3];
-  return V / 2 < (1LL << 30);  // half-volumes and plane indices stay in 32 bits
+  // half-volumes and plane indices stay in 32 bits: V < 2^31
+  return lattice_sites_checked(d, (1LL << 31) - 1) > 0;
 }
 
 int tiles_for(const int* d, int threads) {

@@ -47,6 +47,20 @@ struct LatDev {
   unsigned int mx, my;  // ceil(2^32 / Lx), ceil(2^32 / Ly): n / L = umulhi(n, m) for n L < 2^32
 };
 
+// Number of sites of a lattice with extents d[0..3], or -1 when an extent is below 1
+// or the product exceeds max_sites.  Every partial product is compared with max_sites
+// before the next multiplication (by division), so no intermediate value can overflow
+// whatever the extents are (host code: creation checks and the allocation-free call).
+inline long long lattice_sites_checked(const int* d, long long max_sites) {
+  long long v = 1;
+  for (int k = 0; k < 4; ++k) {
+    if (d[k] < 1) return -1;
+    if ((long long)d[k] > max_sites / v) return -1;
+    v *= d[k];
+  }
+  return v;
+}
+
 // One block of sites of one lattice, one time slice: (lat, t, first h3, unit)
 // (int4 tiles in device memory).
 

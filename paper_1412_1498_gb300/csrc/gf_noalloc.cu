@@ -165,24 +165,27 @@ extern "C" GF_API int gf_functional_theta_noalloc(const int dims[4], int gauge, 
     g_error = "gauge must be GF_LANDAU or GF_COULOMB";
     return GF_EINVAL;
   }
-  long long V = 1;
   for (int k = 0; k < 4; ++k) {
     if (dims[k] < 2 || dims[k] % 2 != 0) {
       g_error = "every extent must be even and >= 2";
       return GF_EINVAL;
     }
-    V *= dims[k];
   }
   if (((uintptr_t)links % 16) != 0) {
     g_error = "links must be 16-byte aligned device memory";
     return GF_EINVAL;
   }
-  const long long blocks = (V + kThreads - 1) / kThreads;
-  if (blocks > GF_NOALLOC_MAX_BLOCKS) {
-    g_error = "lattice too large for the static scratch: at most " +
-              std::to_string((long long)GF_NOALLOC_MAX_BLOCKS * kThreads) + " sites (got " + std::to_string(V) + ")";
+  // the volume is formed with an overflow check against the scratch's site limit, so
+  // no extents (each below 2^31, any product) can reach the launch below
+  const long long max_sites = (long long)GF_NOALLOC_MAX_BLOCKS * kThreads;
+  const long long V = gf::lattice_sites_checked(dims, max_sites);
+  if (V < 0) {
+    g_error = "lattice too large for the static scratch: at most " + std::to_string(max_sites) +
+              " sites (got " + std::to_string(dims[0]) + " x " + std::to_string(dims[1]) + " x " +
+              std::to_string(dims[2]) + " x " + std::to_string(dims[3]) + ")";
     return GF_EINVAL;
   }
+  const long long blocks = (V + kThreads - 1) / kThreads;
   double* scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != GF_OK) return rc;

@@ -120,3 +120,25 @@ def test_header_is_plain_c_and_links(tmp_path):
     assert out.returncode == 0, out.stderr
     rc, nbytes, n = out.stdout.split()
     assert rc == "0" and int(nbytes) > 0 and int(n) == len(names)
+
+
+# extents whose int64 product wraps negative (1102 * 4664 * 6944 * 516856348 > 2^63):
+# every volume check must reject them before any CUDA call
+WRAP_DIMS = (1102, 4664, 6944, 516856348)
+
+
+def test_wrapping_volume_rejected_by_creation():
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_workspace_bytes([WRAP_DIMS], gf.GF_LANDAU, gf.GF_FP32_12)
+    assert e.value.code == gf.GF_EINVAL
+    assert "2^31" in gf.gf_last_error(None)
+
+
+@pytest.mark.parametrize("dims", [WRAP_DIMS, (2, 2, 2, 2 ** 30), (65536, 65536, 2, 2)])
+def test_noalloc_rejects_wrapping_or_oversized_volume_on_the_host(dims):
+    # the argument checks come before any CUDA call, so this runs without a GPU; the
+    # links pointer is a dummy (aligned, never dereferenced)
+    with pytest.raises(gf.GFError) as e:
+        gf.gf_functional_theta_noalloc(dims, gf.GF_LANDAU, 256, 512)
+    assert e.value.code == gf.GF_EINVAL
+    assert "too large" in gf.gf_last_error(None)
