@@ -314,8 +314,10 @@ struct gf_handle {
                 // 2: polish buffer in double-float (only inside gf_fix)
   int phase_sweeps[2] = {0, 0};
   int sweeps_done = 0;  // since the last upload: the reunitarisation / check schedule
-  // graphs: one per buffer state (OR), one for Fourier acceleration
+  // graphs: one per buffer state (OR), one per set of precision levels of a mixed run,
+  // one for Fourier acceleration
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph_mix[8] = {};
   cudaGraphExec_t graph_fasd = nullptr;
   std::string err;
 };
@@ -342,6 +344,11 @@ void drop_graphs(gf_handle* h) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  for (auto& g : h->graph_mix)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   if (h->graph_fasd) {
     cudaGraphExecDestroy(h->graph_fasd);
     h->graph_fasd = nullptr;
@@ -355,8 +362,11 @@ char* cur_links(const gf_handle* h) { return h->cur >= 1 ? h->links64 : h->links
 LatDev* cur_lats(const gf_handle* h) { return h->cur >= 1 ? h->d_lats64 : h->d_lats; }
 const LatDev& cur_lat_host(const gf_handle* h, int l) { return h->cur >= 1 ? h->lats64[l] : h->lats[l]; }
 
-// Build the tile table for the current block size and upload it.
-int build_tiles(gf_handle* h) {
+// Build the tile table for the current block size and upload it.  `keep` (nullable)
+// lists per unit whether its tiles go into the table: a mixed run drops the tiles of
+// finished units (their range becomes empty) so that the launches of its last sweeps
+// cover only the units still working.
+int build_tiles(gf_handle* h, const std::vector<int>* keep = nullptr) {
   std::vector<int4> tiles;
   std::vector<int> unit_tiles, unit_lat;
   for (int l = 0; l < h->n_lat; ++l) {
@@ -371,6 +381,7 @@ int build_tiles(gf_handle* h) {
         unit_lat.push_back(l);
       }
       const int unit = lat.unit0 + (h->gauge == GF_COULOMB ? t : 0);
+      if (keep && !(*keep)[unit]) continue;
       for (int h3 = 0; h3 < lat.V3h; h3 += h->threads) tiles.push_back(make_int4(l, t, h3, unit));
     }
   }
@@ -411,6 +422,7 @@ SweepArgs sweep_args(gf_handle* h, int parity, bool loop, int reverse) {
   a.form = h->form;
   a.reunit = 0;
   a.measure = 0;
+  a.level = 1;
   a.omega = h->omega;
   return a;
 }
@@ -429,6 +441,7 @@ MeasureArgs measure_args(gf_handle* h, int parity, bool loop, int reverse) {
   a.part_F = parity == 0 && !loop ? h->d_partF : nullptr;
   a.part_theta = parity == 0 ? h->d_pthe : h->d_ptho;
   a.parity = parity;
+  a.level = 1;
   return a;
 }
 
@@ -534,6 +547,8 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   s.n_active = 0;
   s.ticket = 0;
   s.eps = eps;
+  s.eps_mid = eps;
+  s.final_level = 1;
   s.hist_n = h->hist_n;
   s.hist_base = h->hist_sweeps - offset;
   GF_CK(h, cudaMemcpyAsync(h->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream));
@@ -547,6 +562,218 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   }
   *done = s.sweep - offset;
   h->hist_n = s.hist_n;
+  return GF_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// Mixed precision with a precision level per lattice.  Level 1 is the handle's FP32
+// storage, level 2 the double-float polish copy, level 3 the FP64-18 copy (levels 2 and 3
+// share the polish buffer).  A unit's mask entry is its level while it sweeps, 0 once it
+// is below eps at level 3, and -level once it is below the threshold of a lower level
+// (eps_switch for level 1, eps for level 2).  Between graph replays the host moves every
+// lattice whose units all wait to the next level (a lattice is the unit of storage: the
+// time slices of a Coulomb lattice share its temporal links, which every slice's site
+// updates transform, so they change precision together), and measures the moved units
+// in the new precision before they sweep again.  Each replay runs the kernels of the
+// levels that have sweeping units; a unit that starts waiting in the middle of a replay
+// idles until its end (at most kGraphSweeps - 1 sweeps).
+// ---------------------------------------------------------------------------------
+int level_storage(const gf_handle* h, int L) { return L == 1 ? h->storage : L == 2 ? kSplit18 : GF_FP64_18; }
+char* level_links(const gf_handle* h, int L) { return L == 1 ? h->links : h->links64; }
+LatDev* level_lats(const gf_handle* h, int L) { return L == 1 ? h->d_lats : h->d_lats64; }
+
+SweepArgs sweep_args_level(gf_handle* h, int L, int parity, int reverse) {
+  SweepArgs a = sweep_args(h, parity, true, reverse);
+  a.links = level_links(h, L);
+  a.lats = level_lats(h, L);
+  a.level = L;
+  return a;
+}
+
+// loop: the even-site pass of a check sweep (units the odd part cannot decide);
+// otherwise both parities of the units entering level L (their F from the even pass)
+MeasureArgs measure_args_level(gf_handle* h, int L, int parity, int reverse, bool loop) {
+  MeasureArgs a = measure_args(h, parity, loop, reverse);
+  a.links = level_links(h, L);
+  a.lats = level_lats(h, L);
+  a.active = h->d_pending;
+  a.level = L;
+  if (!loop) a.part_F = parity == 0 ? h->d_partF : nullptr;
+  return a;
+}
+
+// One sweep of the mixed loop over the levels in `mask` (bit L-1 for level L).
+int enqueue_mixed_sweep(gf_handle* h, cudaStream_t s, int* pass, int mask) {
+  for (int parity = 0; parity < 2; ++parity) {
+    const int rev = (*pass)++ & 1;
+    for (int L = 1; L <= 3; ++L)
+      if (mask & (1 << (L - 1))) {
+        launch_sweep(level_storage(h, L), h->nd, h->repro, h->variant, sweep_args_level(h, L, parity, rev),
+                     h->n_tiles, h->threads, s);
+        GF_CK_LAUNCH(h);
+      }
+    if (parity == 1) {
+      launch_finish(finish_args(h, FINISH_ODD), s);
+      GF_CK_LAUNCH(h);
+      for (int L = 1; L <= 3; ++L)
+        if (mask & (1 << (L - 1))) {
+          launch_measure(level_storage(h, L), h->nd, h->variant, measure_args_level(h, L, 0, rev ^ 1, true),
+                         h->n_tiles, h->threads, s);
+          GF_CK_LAUNCH(h);
+        }
+      launch_finish(finish_args(h, FINISH_LOOP), s);
+      GF_CK_LAUNCH(h);
+    }
+  }
+  return GF_OK;
+}
+
+int ensure_mixed_graph(gf_handle* h, int mask) {
+  if (h->graph_mix[mask]) return GF_OK;
+  GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = GF_OK, pass = 0;
+  for (int j = 0; j < kGraphSweeps && rc == GF_OK; ++j) rc = enqueue_mixed_sweep(h, h->cap_stream, &pass, mask);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+  if (rc != GF_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph_mix[mask], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return GF_OK;
+}
+
+// Copy lattice l from level `from` to level `to` (> from).
+int convert_lattice(gf_handle* h, int l, int from, int to) {
+  if (from == 1 && to == 2) {
+    launch_to_split(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
+  } else if (from == 1) {
+    launch_to_fp64(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
+  } else {
+    launch_split_to_fp64(h->links64, h->lats64[l], h->stream);
+  }
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+// Measure the units whose pending entry names the level they just entered (both parities
+// in that level's precision), then FINISH_ENTER decides them and recounts the active units.
+int enqueue_enter(gf_handle* h, const std::vector<int>& pend) {
+  GF_CK(h, cudaMemcpyAsync(h->d_pending, pend.data(), sizeof(int) * pend.size(), cudaMemcpyHostToDevice, h->stream));
+  int levels = 0;
+  for (int v : pend)
+    if (v > 0) levels |= 1 << (v - 1);
+  for (int L = 1; L <= 3; ++L)
+    if (levels & (1 << (L - 1)))
+      for (int parity = 0; parity < 2; ++parity) {
+        launch_measure(level_storage(h, L), h->nd, h->variant, measure_args_level(h, L, parity, parity, false),
+                       h->n_tiles, h->threads, h->stream);
+        GF_CK_LAUNCH(h);
+      }
+  launch_finish(finish_args(h, FINISH_ENTER), h->stream);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+int run_mixed(gf_handle* h, double eps, int budget, int* sweeps_fp32, int* sweeps_polish, int* sweeps) {
+  const bool split = h->polish == GF_POLISH_SPLIT && h->form == GF_OR_FIRST_ORDER;
+  const int nu = h->n_units;
+  std::vector<int> lev(h->n_lat, 1), act(nu), pend(nu);
+  DevState s{};
+  s.sweep = 0;
+  s.limit = budget;
+  s.check_interval = h->check_interval;
+  s.reunit_interval = h->reunit_interval;
+  s.eps = eps;
+  s.eps_mid = std::max(eps, h->eps_switch);
+  s.final_level = 3;
+  s.hist_n = h->hist_n;
+  s.hist_base = 0;
+  GF_CK(h, cudaMemcpyAsync(h->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream));
+  int rc = enqueue_measure_all(h, FINISH_RESET);  // every unit at level 1
+  if (rc != GF_OK) return rc;
+  *sweeps_fp32 = *sweeps_polish = 0;
+  int mask_prev = 0, sweep_prev = 0;
+  // tiles per unit, for the compaction of the tile table as units finish
+  std::vector<long long> unit_ntiles(nu, 0);
+  for (int l = 0; l < h->n_lat; ++l) {
+    const LatDev& d = h->lats[l];
+    const long long per_slice = (d.V3h + h->threads - 1) / h->threads;
+    for (int k = 0; k < d.n_units; ++k) unit_ntiles[d.unit0 + k] = per_slice * (d.L[3] / d.n_units);
+  }
+  bool compacted = false;
+  // the units of lattice l are lats[l].unit0 .. + n_units - 1
+  auto move_lattices = [&](bool to_final) -> int {
+    bool moved = false;
+    std::fill(pend.begin(), pend.end(), 0);
+    for (int l = 0; l < h->n_lat; ++l) {
+      const int L = lev[l], u0 = h->lats[l].unit0, n = h->lats[l].n_units;
+      if (L == 3) continue;
+      bool sweeping = false, waiting = false;
+      for (int u = u0; u < u0 + n; ++u) {
+        sweeping = sweeping || act[u] == L;
+        waiting = waiting || act[u] == -L;
+      }
+      if (!to_final && (sweeping || !waiting)) continue;
+      const int next = to_final ? 3 : (L == 1 && split ? 2 : 3);
+      if (to_final && L == 1 && split) {  // the double-float copy on the way, as a polish would
+        if ((rc = convert_lattice(h, l, 1, 2)) != GF_OK) return rc;
+        if ((rc = convert_lattice(h, l, 2, 3)) != GF_OK) return rc;
+      } else if ((rc = convert_lattice(h, l, L, next)) != GF_OK) {
+        return rc;
+      }
+      for (int u = u0; u < u0 + n; ++u)
+        if (act[u] != 0) act[u] = pend[u] = next;
+      lev[l] = next;
+      moved = true;
+    }
+    if (!moved) return 1;
+    GF_CK(h, cudaMemcpyAsync(h->d_active, act.data(), sizeof(int) * nu, cudaMemcpyHostToDevice, h->stream));
+    if ((rc = enqueue_enter(h, pend)) != GF_OK) return rc;
+    return GF_OK;
+  };
+  for (;;) {
+    GF_CK(h, cudaMemcpyAsync(act.data(), h->d_active, sizeof(int) * nu, cudaMemcpyDeviceToHost, h->stream));
+    if ((rc = read_state(h, &s)) != GF_OK) return rc;
+    if (mask_prev) {
+      const int d = s.sweep - sweep_prev;
+      if (mask_prev & 1) *sweeps_fp32 += d;
+      if (mask_prev & 6) *sweeps_polish += d;
+      mask_prev = 0;
+    }
+    rc = move_lattices(false);
+    if (rc < 0) return rc;
+    if (rc == GF_OK) continue;  // moved units were measured at their new level: read again
+    if (s.n_active == 0 || s.sweep >= s.limit) break;
+    int mask = 0;
+    long long need = 0;
+    for (int u = 0; u < nu; ++u) {
+      if (act[u] > 0) mask |= 1 << (act[u] - 1);
+      if (act[u] != 0) need += unit_ntiles[u];
+    }
+    if (nu > 1 && 2 * need <= h->n_tiles) {  // half the table or more belongs to finished units
+      std::vector<int> keep(nu);
+      for (int u = 0; u < nu; ++u) keep[u] = act[u] != 0;
+      if ((rc = build_tiles(h, &keep)) != GF_OK) return rc;  // drops the captured graphs
+      compacted = true;
+    }
+    if ((rc = ensure_mixed_graph(h, mask)) != GF_OK) return rc;
+    GF_CK(h, cudaGraphLaunch(h->graph_mix[mask], h->stream));
+    mask_prev = mask;
+    sweep_prev = s.sweep;
+  }
+  // every lattice ends in the FP64 copy (what gf_download and the next calls read); the
+  // ones moved here are measured and decided in FP64
+  if (compacted && (rc = build_tiles(h)) != GF_OK) return rc;  // every unit for the final measurement
+  rc = move_lattices(true);
+  if (rc < 0) return rc;
+  if ((rc = read_state(h, &s)) != GF_OK) return rc;
+  h->cur = 1;
+  h->hist_n = s.hist_n;
+  *sweeps = s.sweep;
   return GF_OK;
 }
 
@@ -960,40 +1187,10 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
   }
   const bool mixed = (h->flags & GF_FLAG_MIXED) && h->cur == 0;
   if (mixed) {
-    h->sweeps_done = 0;  // each precision phase keeps its own schedule
-    if ((rc = run_phase(h, std::max(eps, h->eps_switch), maxiter, &done)) != GF_OK) return rc;
-    h->phase_sweeps[0] = done;
-    int done2 = 0;
-    if (h->polish == GF_POLISH_SPLIT && h->form == GF_OR_FIRST_ORDER) {
-      // double-float polish, then FP64 (conversion with an FP64 reunitarisation)
-      for (int l = 0; l < h->n_lat; ++l) {
-        launch_to_split(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
-        GF_CK_LAUNCH(h);
-      }
-      h->cur = 2;
-      h->sweeps_done = 0;
-      h->hist_sweeps = done;
-      rc = run_phase(h, eps, maxiter - done, &done2);
-      for (int l = 0; l < h->n_lat; ++l) {
-        launch_split_to_fp64(h->links64, h->lats64[l], h->stream);
-        GF_CK_LAUNCH(h);
-      }
-      h->cur = 1;
-      if (rc != GF_OK) return rc;
-      done += done2;
-    } else {
-      for (int l = 0; l < h->n_lat; ++l) {
-        launch_to_fp64(h->storage, h->links, h->links64, h->lats[l], h->lats64[l], h->stream);
-        GF_CK_LAUNCH(h);
-      }
-      h->cur = 1;
-    }
-    int done3 = 0;
-    h->sweeps_done = 0;
-    h->hist_sweeps = done;
-    if ((rc = run_phase(h, eps, maxiter - done, &done3)) != GF_OK) return rc;
-    h->sweeps_done = done3;
-    h->phase_sweeps[1] = done2 + done3;
+    // one loop over all precision levels; the reunitarisation and check schedules count
+    // the loop's sweeps from the start of this call
+    if ((rc = run_mixed(h, eps, maxiter, &h->phase_sweeps[0], &h->phase_sweeps[1], &done)) != GF_OK) return rc;
+    h->sweeps_done = done;
   } else {
     if ((rc = run_phase(h, eps, maxiter, &done)) != GF_OK) return rc;
     h->sweeps_done += done;

@@ -78,8 +78,22 @@ struct DevState {
   int sweep_closed;     // the odd-part finish already counted this sweep (nothing pending)
   int hist_n;           // history records written in the current gf_fix
   int hist_base;        // sweep number of the record = hist_base + sweep (across phases)
-  double eps;           // stop threshold of the current phase
+  double eps;           // stop threshold (of the final precision level)
+  double eps_mid;       // threshold of level 1 when it is not the final level (mixed runs)
+  int final_level;      // 1, or 3 in a mixed run (1 FP32 storage, 2 double-float, 3 FP64)
 };
+
+// Stop threshold of a unit at precision level lvl (a mixed run leaves level 1 at the
+// switch threshold, the polish levels at eps).
+__host__ __device__ inline double state_threshold(const DevState* st, int lvl) {
+  return (lvl == 1 && st->final_level > 1) ? st->eps_mid : st->eps;
+}
+// Mask entry of a unit at level lvl after a check that found it below its threshold:
+// done (0) at the final level, otherwise waiting (-lvl) for the host to move its
+// lattice to the next level.
+__host__ __device__ inline int state_mask_below(const DevState* st, int lvl) {
+  return lvl >= st->final_level ? 0 : -lvl;
+}
 
 __host__ __device__ inline bool state_running(const DevState* st) {
   return st->n_active > 0 && st->sweep < st->limit;

@@ -44,15 +44,17 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   // kernel is short and its time is mostly dependent round trips to memory.
   const int n_active = a.st->n_active, sweep = a.st->sweep, limit = a.st->limit;
   const int ci = a.st->check_interval, closed = a.st->sweep_closed;
-  const double eps = a.st->eps;
-  const bool was_active = a.active[u] != 0;
+  const double eps = a.st->eps, eps_mid = a.st->eps_mid;
+  const int final_level = a.st->final_level;
+  const int lvl_in = a.active[u];  // > 0: sweeping at that precision level
+  const bool was_active = lvl_in > 0;
   const bool pend_in = a.pending[u] != 0;
   const int tb = a.n_units == 1 ? 0 : a.unit_tiles[u];
   const int te = a.n_units == 1 ? a.n_tiles : a.unit_tiles[u + 1];
   // The first pass of tile partials: with one unit its range is a kernel argument, so
   // these loads wait for nothing and travel with the ones above.  (FINISH_LOOP, which
   // mostly has nothing to add, loads inside the reduction.)
-  const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET;
+  const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET || a.mode == FINISH_ENTER;
   const bool early = a.mode != FINISH_LOOP;
   const float2* p1 = a.mode == FINISH_ODD ? a.part_th_odd : a.part_th_even;
   float2 x0[kFinishUnroll], x1[kFinishUnroll], x2[kFinishUnroll];
@@ -86,6 +88,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   bool reduce;
   if (a.mode == FINISH_ODD) reduce = was_active;
   else if (a.mode == FINISH_LOOP) reduce = check && was_active && pend_in;
+  else if (a.mode == FINISH_ENTER) reduce = pend_in;
   else reduce = true;
   if (reduce) {
     float2 acc0 = make_float2(0.f, 0.f), acc1 = acc0, acc2 = acc0;
@@ -136,15 +139,18 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
     double uF = uF_old, uT = uT_old;
     int pend = 0;
     bool act = was_active;
+    // the unit's precision level (a reset starts every unit at level 1) and its threshold
+    const int lvl = a.mode == FINISH_RESET ? 1 : lvl_in;
+    const double thr = (lvl == 1 && final_level > 1) ? eps_mid : eps;
     if (a.mode == FINISH_ODD) {
       if (reduce) {
         uF = s0;
         a.unit_sumF[u] = s0;
         a.unit_F[u] = s0 * invF;
         a.unit_sumTh_odd[u] = s1;
-        pend = forced || a.hist != nullptr || !(s1 * invT >= eps);  // a history wants every theta
+        pend = forced || a.hist != nullptr || !(s1 * invT >= thr);  // a history wants every theta
       }
-      a.pending[u] = pend;
+      a.pending[u] = pend ? lvl : 0;  // the even-site pass of this level serves the unit
     } else {
       if (reduce) {
         uT = a.mode == FINISH_LOOP ? s1 + uTo : s1 + s2;
@@ -156,9 +162,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
           a.unit_F[u] = s0 * invF;
         }
         if (a.mode != FINISH_MEASURE) {
-          act = uT * invT >= eps;
-          a.active[u] = act;
+          act = uT * invT >= thr;
+          a.active[u] = act ? lvl : (lvl >= final_level ? 0 : -lvl);
         }
+        if (a.mode == FINISH_ENTER) a.pending[u] = 0;
       }
       if (a.mode == FINISH_LOOP && was_active) a.iters[u] += 1;
     }
@@ -197,7 +204,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   // the loop state: counts, lattice totals in a fixed order
   int cnt = 0;  // ODD: pending units; otherwise: active units
   for (int v = tid; v < a.n_units; v += blockDim.x)
-    cnt += a.mode == FINISH_ODD ? __ldcg(a.pending + v) : __ldcg(a.active + v);
+    cnt += a.mode == FINISH_ODD ? (__ldcg(a.pending + v) != 0) : (__ldcg(a.active + v) > 0);
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
   __syncthreads();
@@ -213,7 +220,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   }
   if (a.mode == FINISH_ODD)  // nothing pending: every active unit continues; close the sweep
     for (int v = tid; v < a.n_units; v += blockDim.x)
-      if (__ldcg(a.active + v) != 0) a.iters[v] += 1;
+      if (__ldcg(a.active + v) > 0) a.iters[v] += 1;
   if (!loop || check) {
     for (int l = tid; l < a.n_lat; l += blockDim.x) {
       const LatDev lat = a.lats[l];

@@ -216,7 +216,8 @@ struct SweepArgs {
   char* links;
   const LatDev* lats;
   const int4* tiles;       // (lat, t, first h3, unit) per block
-  const int* active;       // per unit (nullable: all active)
+  const int* active;       // per unit (nullable: all units): a tile runs when its unit's
+                           // entry equals `level`
   const DevState* st;      // nullable; when set, the loop state decides everything
   float2* part_theta;      // per tile: theta partial of the updated (odd) sites (hi, lo)
   float2* part_F;          // nullable; per tile: Re Tr of the updated sites' 2 nd links
@@ -226,6 +227,7 @@ struct SweepArgs {
   int measure;             // used when st == nullptr
   int n_tiles;
   int reverse;             // walk the tiles last to first (L2 reuse across passes)
+  int level;               // precision level these tiles must carry in `active` (1 unless mixed)
   double omega;
 };
 
@@ -233,13 +235,14 @@ struct MeasureArgs {
   const char* links;
   const LatDev* lats;
   const int4* tiles;
-  const int* active;       // nullable
+  const int* active;       // nullable; a tile runs when its unit's entry equals `level`
   const DevState* st;      // nullable; when set, only runs on check sweeps
   float2* part_F;          // nullable: per tile sum of Re Tr over the 2 nd links of each site
   float2* part_theta;      // per tile sum of Tr[Delta Delta^+] (pairs hi, lo)
   int parity;
   int n_tiles;
   int reverse;
+  int level;
 };
 
 constexpr int kFinishThreads = 256;  // threads of a finishing block (one block per unit)
@@ -249,13 +252,15 @@ struct FinishArgs {
   const LatDev* lats;
   const int* unit_tiles;   // n_units + 1 tile boundaries
   int n_tiles;             // tiles of the table (the single unit's range when n_units == 1)
-  int* pending;            // per unit: this check needs the even-site pass (FINISH_ODD sets it)
+  int* pending;            // per unit: the unit's level when this check needs the even-site
+                           // pass (FINISH_ODD sets it), or when FINISH_ENTER is to measure it
   double* hist;            // nullable: records (sweep, F and theta of every lattice) of each check
   int hist_cap;            // records hist can hold
   double* unit_sumTh_odd;  // per unit: odd-site part of the theta sum of the current check
   const int* unit_lat;     // lattice of each unit
   const double* unit_norm;  // per unit 1 / (nd Nc sites), 1 / (Nc sites): F and theta of Eqs. (1), (2)
-  int* active;
+  int* active;             // per unit: level (> 0) while sweeping, 0 done, -level when the
+                           // unit reached the threshold of a level below the final one
   int* iters;
   const float2* part_F;    // per-tile partials as pairs (hi, lo)
   const float2* part_th_even;
@@ -270,10 +275,10 @@ struct FinishArgs {
   int n_units;
   int n_lat;
   int nd;
-  int mode;                // FINISH_LOOP, FINISH_MEASURE, FINISH_RESET
+  int mode;                // FINISH_LOOP, FINISH_MEASURE, FINISH_RESET, FINISH_ODD, FINISH_ENTER
 };
 
-enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2, FINISH_ODD = 3 };
+enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2, FINISH_ODD = 3, FINISH_ENTER = 4 };
 
 // Fourier-accelerated steepest descent (kernels in gf_fasd.cuh)
 struct FasdArgs {
@@ -348,7 +353,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
   }
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
-  if (a.active && !a.active[tile.w]) return;
+  if (a.active && a.active[tile.w] != a.level) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
   T q = T(0), fs = T(0);
@@ -453,7 +458,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
-  if (a.active && !a.active[tile.w]) return;
+  if (a.active && a.active[tile.w] != a.level) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
   T fsum = T(0), q = T(0);

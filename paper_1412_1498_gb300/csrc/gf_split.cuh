@@ -245,7 +245,7 @@ __device__ __forceinline__ float split_theta_site(const acc2 (&A)[18]) {
 
 // ------------------------------------------------------------------------- the sweep
 template <int ND>
-__global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
+__global__ void __launch_bounds__(256) k_or_sweep_split(SweepArgs a) {
   __shared__ double red[64];
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
   }
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
-  if (a.active && !a.active[tile.w]) return;
+  if (a.active && a.active[tile.w] != a.level) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
   float q = 0.f, fsum = 0.f;
@@ -394,12 +394,12 @@ __global__ void __launch_bounds__(128) k_or_sweep_split(SweepArgs a) {
 
 // ------------------------------------------------------------------------- measurement
 template <int ND>
-__global__ void __launch_bounds__(128) k_measure_split(MeasureArgs a) {
+__global__ void __launch_bounds__(256) k_measure_split(MeasureArgs a) {
   __shared__ double red[64];
   if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
-  if (a.active && !a.active[tile.w]) return;
+  if (a.active && a.active[tile.w] != a.level) return;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
   float fsum = 0.f, q = 0.f;

@@ -41,7 +41,7 @@ __device__ __forceinline__ PipeSite pipe_issue(const SweepArgs& a, int k, int bu
   ps.ti = a.reverse ? a.n_tiles - 1 - k : k;
   const int4 tile = a.tiles[ps.ti];
   ps.lat = tile.x;
-  ps.active = a.active == nullptr || a.active[tile.w] != 0;
+  ps.active = a.active == nullptr || a.active[tile.w] == a.level;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
   ps.valid = ps.active && h3 < lat.V3h;
@@ -174,7 +174,7 @@ __device__ __forceinline__ MeasSite meas_issue(const MeasureArgs& a, int k, int 
   MeasSite ms;
   ms.ti = a.reverse ? a.n_tiles - 1 - k : k;
   const int4 tile = a.tiles[ms.ti];
-  ms.active = a.active == nullptr || a.active[tile.w] != 0;
+  ms.active = a.active == nullptr || a.active[tile.w] == a.level;
   const LatDev lat = a.lats[tile.x];
   const int h3 = tile.z + (int)threadIdx.x;
   ms.valid = ms.active && h3 < lat.V3h;
