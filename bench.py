@@ -15,10 +15,11 @@ CUDA-event duration, against the measured HBM copy bandwidth, with ncu's DRAM by
 launch when the profiled source is unchanged), the same metric end to end through the
 C ABI with pinned host buffers, time to theta < 1e-15 for pure FP64 and for mixed
 FP32 -> FP64 and FP32 -> double-float -> FP64 fixing, the double-float polish sweep,
-Fourier-accelerated steepest descent, the differentiable F/theta, optionally the
-batched Coulomb-slice and ensemble workloads, and the CPU oracle on the host cores.
+Fourier-accelerated steepest descent, the differentiable F/theta, the batched
+Coulomb-slice and ensemble workloads (throughput, and time until every unit is below
+theta = 1e-15), SM clocks over the whole GPU arm, and the CPU oracle on the host cores.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--units-probe]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--skip-units]
 """
 from __future__ import annotations
 
@@ -95,20 +96,43 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def nvsmi_id(device) -> str:
+    """nvidia-smi's name for the CUDA device `device` of this process.  nvidia-smi ignores
+    CUDA_VISIBLE_DEVICES, so a CUDA ordinal may name another GPU there: the device's UUID
+    (or, failing that, its PCI bus id) names the same physical GPU in both."""
+    import torch
+    props = torch.cuda.get_device_properties(device)
+    uuid = getattr(props, "uuid", None)
+    if uuid is not None:
+        u = str(uuid)
+        return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    bus = getattr(props, "pci_bus_id", None)
+    if bus is not None:
+        dom = getattr(props, "pci_domain_id", 0)
+        dev = getattr(props, "pci_device_id", 0)
+        return f"{dom:08x}:{bus:02x}:{dev:02x}.0"
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    idx = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+    parts = [p for p in vis.split(",") if p.strip()]
+    return parts[idx].strip() if idx < len(parts) else str(idx)
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+    """nvidia-smi samples (every 100 ms) of SM clock and throttle reasons, with the time
+    each arrived, from before the warm-up to the end of the GPU arm."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index, self.proc, self.lines = index, None, []
+    def __init__(self, gpu_id: str):
+        self.gpu_id, self.proc, self.lines = gpu_id, None, []
+        self.windows = {}
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
@@ -119,7 +143,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, name: str, t0: float, t1: float):
+        """Remember a wall-clock window (perf_counter seconds) to summarise on its own."""
+        self.windows[name] = (t0, t1)
 
     def __exit__(self, *exc):
         if self.proc:
@@ -130,10 +158,13 @@ class ClockSampler:
                 self.proc.kill()
             self.t.join(timeout=2)
 
-    def summary(self):
+    def summary(self, window: str | None = None):
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for line in self.lines:
+        lo, hi = self.windows.get(window, (-1e300, 1e300)) if window else (-1e300, 1e300)
+        for when, line in self.lines:
+            if not (lo <= when <= hi):
+                continue
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 8:
                 continue
@@ -209,12 +240,20 @@ def run_reference(args):
     }))
 
 
-def units_probe(gf, dev, stream, n_coulomb: int = 400, n_ensemble: int = 200):
-    """Throughput of the batched-unit workloads (FP32-12 sweeps with the stop check after
-    every sweep, eps = 1e-300 so every unit stays active, autotuned launch shape): the
-    Coulomb 32^3 x 64 field (eps 0.5, seed 4) with its 64 time slices as units, and the
-    48-lattice ensemble (16 x 16^4, 16 x 24^4, 16 x 16^3 x 32; eps ~ U[0.3, 0.6], seeds
-    100-147) in one batch.  Link bytes are counted as 16 V b per sweep."""
+UNITS_SWITCH = 1e-11   # FP32 -> double-float switch of the batched runs (FP32 floor ~1e-13)
+UNITS_BUDGET = 200000  # loop sweeps allowed to the batched runs
+
+
+def units_leg(gf, dev, stream, peak: float, n_coulomb: int = 400, n_ensemble: int = 200):
+    """The batched-unit workloads: the Coulomb 32^3 x 64 field (eps 0.5, seed 4) with its 64
+    time slices as convergence units, and the 48-lattice ensemble (16 x 16^4, 16 x 24^4,
+    16 x 16^3 x 32; eps ~ U[0.3, 0.6], seeds 100-147) in one batch.
+
+    Throughput: FP32-12 sweeps with the stop check after every sweep (eps = 1e-300, so every
+    unit stays active; autotuned launch shape); link bytes counted as 16 V b per sweep,
+    against the measured HBM copy bandwidth.  Time to theta < 1e-15 on every unit: mixed
+    FP32-12 -> double-float -> FP64 (each lattice changes precision when its own units
+    reach the switch), wall time of gf_fix from the uploaded field, every unit checked."""
     import torch
     from paper_1412_1498_gb300 import fields
 
@@ -226,40 +265,64 @@ def units_probe(gf, dev, stream, n_coulomb: int = 400, n_ensemble: int = 200):
         b.synchronize()
         return a.elapsed_time(b) / n
 
+    def throughput(dims_list, gauge, Us, n):
+        fx = gf.GaugeFixer(dims_list, gauge, gf.GF_FP32_12, device=dev)
+        up = lambda: [fx.upload(Ui, i) for i, Ui in enumerate(Us)]  # noqa: E731
+        up()
+        t, v = gf.gf_autotune(fx.h)
+        up()
+        gf.gf_fix(fx.h, 1e-300, 5)                 # graph capture
+        up()
+        ms = timed(fx.h, n)
+        fx.close()
+        return ms, t, v
+
+    def to_theta(dims_list, gauge, Us, threads, variant):
+        fx = gf.GaugeFixer(dims_list, gauge, gf.GF_FP32_12, mixed=True, device=dev)
+        gf.gf_set_polish(fx.h, gf.GF_POLISH_SPLIT)
+        gf.gf_set_mixed_switch(fx.h, UNITS_SWITCH)
+        gf.gf_set_block_size(fx.h, threads)
+        gf.gf_set_sweep_variant(fx.h, variant)
+        for i, Ui in enumerate(Us):
+            fx.upload(Ui, i)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fx.fix(1e-15, UNITS_BUDGET)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        _, _, _, uT = fx.functional_theta()
+        fx.close()
+        its = r["iters"]
+        return {"seconds": el, "converged_units": int((uT < 1e-15).sum()), "units": int(len(uT)),
+                "rc": int(r["rc"]), "loop_sweeps": int(its.max()), "unit_sweeps": int(its.sum()),
+                "unit_sweeps_min_median_max": [int(its.min()), int(np.median(its)), int(its.max())],
+                "sweeps_with_fp32_units": int(r["phase_sweeps"][0]),
+                "sweeps_with_polish_units": int(r["phase_sweeps"][1]),
+                "theta_max": float(uT.max()), "switch": UNITS_SWITCH, "budget": UNITS_BUDGET}
+
     out = {}
     dims = (32, 32, 32, 64)
-    U = make_field(dims, EPS_FIELD, 4)
-    fx = gf.GaugeFixer(dims, gf.GF_COULOMB, gf.GF_FP32_12, device=dev)
-    fx.upload(U)
-    gf.gf_autotune(fx.h)
-    fx.upload(U)
-    gf.gf_fix(fx.h, 1e-300, 5)                    # graph capture
-    fx.upload(U)
-    ms = timed(fx.h, n_coulomb)
+    Uc = [make_field(dims, EPS_FIELD, 4)]
+    ms, t, v = throughput([dims], gf.GF_COULOMB, Uc, n_coulomb)
     vol = 32 * 32 * 32 * 64
-    out["coulomb_32x32x32x64"] = {"sweeps": n_coulomb, "ms_per_sweep": ms, "slice_sweeps_per_s": 64e3 / ms,
-                                  "link_GBps": 16 * vol * LINK_B / (ms * 1e-3) / 1e9}
-    fx.close()
-    del fx, U
+    gbps = 16 * vol * LINK_B / (ms * 1e-3) / 1e9
+    out["coulomb_32x32x32x64"] = {
+        "sweeps": n_coulomb, "ms_per_sweep": ms, "slice_sweeps_per_s": 64e3 / ms, "link_GBps": gbps,
+        "roofline_frac": gbps / peak, "block_threads": t, "sweep_kernel": {1: "register", 2: "pipelined"}.get(v, v),
+        "time_to_theta_1e-15": to_theta([dims], gf.GF_COULOMB, Uc, t, v)}
+    del Uc
     dims_list = [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 24)] * 16 + [(16, 16, 16, 32)] * 16
     Us = fields.ensemble(dims_list, list(range(100, 148)))
-    fb = gf.GaugeFixer(dims_list, gf.GF_LANDAU, gf.GF_FP32_12, device=dev)
-
-    def upload_all():
-        for i, Ui in enumerate(Us):
-            fb.upload(Ui, i)
-
-    upload_all()
-    gf.gf_autotune(fb.h)
-    upload_all()
-    gf.gf_fix(fb.h, 1e-300, 5)
-    upload_all()
-    ms = timed(fb.h, n_ensemble)
+    ms, t, v = throughput(dims_list, gf.GF_LANDAU, Us, n_ensemble)
     vtot = sum(d[0] * d[1] * d[2] * d[3] for d in dims_list)
-    out["ensemble_48"] = {"sweeps": n_ensemble, "ms_per_sweep": ms, "unit_sweeps_per_s": 48e3 / ms,
-                          "site_updates_per_s": vtot * 1e3 / ms,
-                          "link_GBps": 16 * vtot * LINK_B / (ms * 1e-3) / 1e9}
-    fb.close()
+    gbps = 16 * vtot * LINK_B / (ms * 1e-3) / 1e9
+    tt = to_theta(dims_list, gf.GF_LANDAU, Us, t, v)
+    tt["unit_sweeps_per_s"] = tt["unit_sweeps"] / tt["seconds"]
+    out["ensemble_48"] = {
+        "sweeps": n_ensemble, "ms_per_sweep": ms, "unit_sweeps_per_s": 48e3 / ms,
+        "site_updates_per_s": vtot * 1e3 / ms, "link_GBps": gbps, "roofline_frac": gbps / peak,
+        "block_threads": t, "sweep_kernel": {1: "register", 2: "pipelined"}.get(v, v),
+        "time_to_theta_1e-15": tt}
     return out
 
 
@@ -311,6 +374,10 @@ def run_gpu(args):
         best = gf.gf_autotune(fx.h)
     fx.upload(U)
 
+    # ---- clock samples from here to the end of the GPU arm (the timed region of a short
+    # run is shorter than one sampling period; its own window is summarised too)
+    clocks = ClockSampler(nvsmi_id(dev)).__enter__()
+
     # ---- warm-up steps (untimed)
     if args.warmup:
         gf.gf_fix(fx.h, 1e-300, args.warmup)
@@ -318,23 +385,26 @@ def run_gpu(args):
     barrier()
 
     # ---- timed region: K steps through gf_fix (device-driven loop, CUDA graphs)
-    with ClockSampler(local) as clocks:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        barrier()
-        e0.record(stream)
-        rc, iters, F, th = gf.gf_fix(fx.h, 1e-300, args.steps)
-        e1.record(stream)
-        barrier()
-        ms_total = e0.elapsed_time(e1)
-        # roofline: the half-sweep kernel alone, back to back on the same stream
-        n_half = 2 * max(20, args.steps // 2)
-        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        k0.record(stream)
-        for _ in range(n_half // 2):
-            fx.or_sweep(2, OMEGA)
-        k1.record(stream)
-        k1.synchronize()
-        half_ms = k0.elapsed_time(k1) / n_half
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    w0 = time.perf_counter()
+    e0.record(stream)
+    rc, iters, F, th = gf.gf_fix(fx.h, 1e-300, args.steps)
+    e1.record(stream)
+    barrier()
+    clocks.mark("timed", w0, time.perf_counter())
+    ms_total = e0.elapsed_time(e1)
+    # roofline: the half-sweep kernel alone, back to back on the same stream
+    n_half = 2 * max(20, args.steps // 2)
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    w0 = time.perf_counter()
+    k0.record(stream)
+    for _ in range(n_half // 2):
+        fx.or_sweep(2, OMEGA)
+    k1.record(stream)
+    k1.synchronize()
+    clocks.mark("roofline", w0, time.perf_counter())
+    half_ms = k0.elapsed_time(k1) / n_half
     assert int(iters[0]) == args.steps, (iters, args.steps)
     # the last sweep of the budget always takes the exact (even-site) check
     bytes_per_step = STEP_BYTES + CHECK_BYTES / args.steps
@@ -450,10 +520,11 @@ def run_gpu(args):
         f5.close()
         del f5
 
-    # ---- batched units: Coulomb time slices, the 48-lattice ensemble (opt-in)
-    units = units_probe(gf, dev, stream) if args.units_probe else None
-
     peak, peak_kind = measured_peaks()
+
+    # ---- batched units: Coulomb time slices, the 48-lattice ensemble
+    units = None if args.skip_units else units_leg(gf, dev, stream, peak)
+    clocks.__exit__(None, None, None)
     achieved = HALF_SWEEP_BYTES / (half_ms * 1e-3) / 1e9
     traffic = None
     if best[1] == gf.GF_SWEEP_PIPELINED:
@@ -478,6 +549,15 @@ def run_gpu(args):
                "kind": "oracle", "sample": f"{n} steps of the full 32^4 workload in {el:.1f} s "
                                             "(FP64 oracle, 18 reals per link, OpenMP over one parity)"}
 
+    clock_line = clocks.summary()
+    timed = clocks.summary("timed")
+    clock_line["gpu"] = clocks.gpu_id
+    clock_line["scope"] = "whole GPU arm: warm-up, timed steps, roofline and every extra leg"
+    clock_line["timed_region"] = {"samples": timed["samples"], "sm_mhz": timed["sm_mhz"],
+                                  "reasons": timed["reasons"], "ms": ms_total}
+    if clock_line["sm_mhz"]:
+        # clock-normalised step cost: SM cycles per step at the arm's median clock
+        clock_line["mcycles_per_step"] = ms_step * 1e-3 * clock_line["sm_mhz"]
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -495,12 +575,12 @@ def run_gpu(args):
                     "d2h_bytes_per_step": canon_bytes},
             "gpu_launches": launches,
             "sweeps_per_s": world * args.steps / (ms_total * 1e-3),
-            "clocks": clocks.summary(),
+            "clocks": clock_line,
             "time_to_theta_1e-15": ttt,
             "split_polish_probe": split_probe,
             "fa_sd": fasd,
             "autograd": autograd,
-            "units_probe": units,
+            "units": units,
         }
         print(json.dumps(line))
     fx.close()
@@ -522,8 +602,8 @@ def main():
     # 63 iterations and the final measurement fill four 16-iteration graph replays exactly
     ap.add_argument("--fasd-iters", type=int, default=63)
     ap.add_argument("--autograd", type=int, default=1)
-    ap.add_argument("--units-probe", action="store_true",
-                    help="also time the Coulomb 32^3x64 slices and the 48-lattice ensemble")
+    ap.add_argument("--skip-units", action="store_true",
+                    help="skip the Coulomb 32^3x64 slice and 48-lattice ensemble leg")
     ap.add_argument("--launch", default="", help="fixed launch shape THREADS:register|pipelined "
                     "instead of the autotuner (for profiler runs)")
     args = ap.parse_args()

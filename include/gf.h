@@ -73,9 +73,10 @@ extern "C" {
 #define GF_FP64_8 5  /* the same 8 reals in FP64 */
 
 /* creation flags */
-#define GF_FLAG_MIXED 1 /* keep an FP64-18 copy: gf_fix runs the FP32 storage down to the
-                           switch threshold, converts, then polishes in FP64 (ignored for
-                           the FP64 storages) */
+#define GF_FLAG_MIXED 1 /* keep a polish copy (144 bytes per link): gf_fix runs the FP32
+                           storage down to the switch threshold, converts, then polishes
+                           (double-float, then FP64; see gf_set_polish) (ignored for the
+                           FP64 storages) */
 #define GF_FLAG_AUTOGRAD 4 /* add the buffers of gf_ad_functional / gf_ad_backward (one
                               lattice, GF_FP64_18) */
 #define GF_FLAG_FASD 2  /* add the buffers of Fourier-accelerated steepest descent (one
@@ -189,11 +190,21 @@ GF_API int gf_reunitarize(gf_handle *h);
  * from the last upload (gf_get_sweeps_done).
  *   eps > 0; maxiter >= 0.  iters (nullable): gf_num_units ints, sweeps each unit
  *   received.  F, theta (nullable): n_lat final values.
- *   With GF_FLAG_MIXED: FP32 sweeps until every unit has theta < the switch threshold
- *   (gf_set_mixed_switch, default 1e-8) or maxiter, then conversion to FP64-18 with a
- *   reunitarisation, then FP64 sweeps until theta < eps; iters counts both phases.
- *   Returns GF_OK when every unit converged, GF_ENOTCONVERGED at maxiter.
- *   Synchronises the stream.
+ *   With GF_FLAG_MIXED each lattice has its own precision level: FP32 sweeps until all
+ *   its units have theta < the switch threshold (gf_set_mixed_switch, default 1e-8),
+ *   then its links are converted (with an FP64 reunitarisation) to the polish
+ *   (gf_set_polish), whose sweeps run until its units have theta < eps, and finally to
+ *   FP64-18, where theta is measured again and FP64 sweeps continue until it is below
+ *   eps.  Lattices of a batch move on independently (a unit below its level's threshold
+ *   waits for the other units of its lattice: the time slices of a Coulomb lattice share
+ *   its temporal links and change precision together); a moved lattice is measured at
+ *   its new level before it sweeps.  One launch per half-sweep and level covers every
+ *   lattice at that level; a lattice that becomes ready in the middle of a CUDA-graph
+ *   replay of 16 sweeps moves at the end of that replay.  At exit every lattice is in
+ *   the FP64 copy (download and gf_functional_theta read it).  iters counts a unit's
+ *   sweeps at every level; maxiter bounds the sweeps of the whole call, whose
+ *   reunitarisation and check schedules count from 0.  Returns GF_OK when every unit
+ *   converged, GF_ENOTCONVERGED at maxiter.  Synchronises the stream.
  */
 GF_API int gf_fix(gf_handle *h, double eps, int maxiter, int *iters, double *F, double *theta);
 
@@ -251,12 +262,14 @@ GF_API int gf_set_block_size(gf_handle *h, int threads);      /* [128]; 64, 128 
    = PIPELINED for FP32-12; other storages always use the register kernel, and asking
    them for PIPELINED returns GF_EINVAL. */
 /* Arithmetic of the polish phase of a mixed-precision gf_fix (GF_FLAG_MIXED):
-   GF_POLISH_FP64 [default]: FP64-18 sweeps.
-   GF_POLISH_SPLIT: double-float sweeps (each real an unevaluated sum of two floats, about
-   48-bit precision, no FP64 arithmetic in the sweep) with the first-order
+   GF_POLISH_SPLIT [default]: double-float sweeps (each real an unevaluated sum of two
+   floats, about 48-bit precision, no FP64 arithmetic in the sweep) with the first-order
    overrelaxation form, then conversion to FP64-18 with an FP64 reunitarisation and
-   FP64 sweeps until theta, measured in FP64, is below eps.  With GF_OR_EXACT the FP64
-   polish is used. */
+   FP64 sweeps until theta, measured in FP64, is below eps.  The polish sweep moves 3x
+   the bytes of an FP32-12 sweep at the memory bandwidth, where an FP64-18 sweep is
+   bound by the FP64 pipe (about 7x slower on this GPU), so this is the default.  With
+   GF_OR_EXACT the FP64 polish is used.
+   GF_POLISH_FP64: FP64-18 sweeps straight after the FP32 phase. */
 #define GF_POLISH_FP64 0
 #define GF_POLISH_SPLIT 1
 GF_API int gf_set_polish(gf_handle *h, int polish);
@@ -279,12 +292,14 @@ GF_API int gf_autotune(gf_handle *h, int *threads_out, int *variant_out);
    from that count (the sweep after n sweeps is sweep n + 1).  To resume a run: download
    the links, read the count, later upload the links into a handle with the same settings
    and set the count; the continued run gives the bits of the uninterrupted one (FP64-18,
-   or any storage in non-mixed mode).  Mixed-precision gf_fix restarts the count in each
-   precision phase.  Upload resets it to 0. */
+   or any storage in non-mixed mode).  Mixed-precision gf_fix counts from 0 over all its
+   precision levels and leaves the count at the sweeps it did.  Upload resets it to 0. */
 GF_API int gf_get_sweeps_done(const gf_handle *h, int *n);
 GF_API int gf_set_sweeps_done(gf_handle *h, int n);
 
-/* Sweeps done by the last gf_fix in the FP32 and FP64 phases (mixed mode), nullable. */
+/* Sweeps of the last gf_fix in which some unit swept at FP32 precision, and in which some
+   unit swept at a polish precision (double-float or FP64), nullable.  With one lattice the
+   two phases follow each other and add up to its sweeps; in a batch they can overlap. */
 GF_API int gf_fix_phase_sweeps(const gf_handle *h, int *fp32_sweeps, int *fp64_sweeps);
 
 /*

@@ -15,7 +15,16 @@ p^2(k) = sum_{mu<nd} 4 sin^2(pi k_mu / L_mu) are the eigenvalues of the lattice
 Laplacian -d^2 (Sec. 1 after Eq. (9)); p^2_max = 4 nd; the k = 0 mode of Delta vanishes
 exactly (Delta is a lattice divergence) and is set to zero.  Landau gauge transforms
 over the four directions, Coulomb gauge over the three spatial ones (separately per
-time slice).  Readings are listed in the design notes.
+time slice).
+
+Readings of the paper used here, each with its reason: the argument of Eq. (7),
+sum_nu Delta_{-nu}[U_nu - U_nu^dagger] - trace, is Delta(x) of Eq. (3) (the same
+expression written with the backward difference of Eq. (9)); Algorithm 2's
+normalisation is the 1/N of the inverse transform (a transform pair must carry it once
+and numpy's inverse does); the first-order exponential with reunitarisation is
+reunit(1 + (alpha/2) Delta~), the exponential's series cut after its linear term
+(Sec. 1 after Eq. (9)); a converged Coulomb slice keeps g = 1 while the others move
+(each slice has its own stop rule, as in the overrelaxation).
 """
 from __future__ import annotations
 

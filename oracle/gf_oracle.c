@@ -17,24 +17,31 @@
  * U + (4*s + mu)*9, row-major 3x3.  Direction mu = 0,1,2,3 is x,y,z,t (time is mu = 3,
  * Section 1 below Eq. (3)).  Boundary conditions are periodic in all four directions.
  *
- * Readings of the paper used here (each is listed with its reason in the design notes):
- *  - nd = 4 directions enter K, F and Delta for Landau gauge, nd = 3 for Coulomb gauge;
- *    F is normalised by 1/(nd*Nc*V) so that the unit field has F = 1.
+ * Readings of the paper used here, each with the reason for it:
+ *  - nd = 4 directions enter K, F and Delta for Landau gauge, nd = 3 for Coulomb gauge
+ *    (Coulomb gauge leaves out the time direction, Section 1 after Eq. (3)).  F is
+ *    normalised by 1/(nd*Nc*V): Eq. (1) prints 1/(4 Nc V) for both gauges, and with nd
+ *    in its place the unit field has F = 1 in either gauge.
  *  - Delta(x) of Eq. (3), literally: A = sum_nu [U_nu(x-nu) - U_nu(x)],
- *    Delta = A - A^dagger - (1/Nc) Tr(A - A^dagger) * 1.
- *  - K(x) of Eq. (5) in its in-place form (the neighbours' g already applied to the
- *    stored links): K = sum_{mu<nd} U_mu(x) + U_mu(x-mu)^dagger.
+ *    Delta = A - A^dagger - (1/Nc) Tr(A - A^dagger) * 1 (the printed "- h.c. - trace",
+ *    with no extra factor: the same expression is the argument of Eq. (7)).
+ *  - K(x) of Eq. (5) in its in-place form: the stored neighbour links already carry
+ *    their own g, so K = sum_{mu<nd} U_mu(x) + U_mu(x-mu)^dagger.
  *  - the SU(3) update is the product of the SU(2)-subgroup maximisers for the index
  *    pairs (0,1), (0,2), (1,2), each computed from the K already rotated by the
- *    previous ones (Section 1, sentence after Eq. (6)).
- *  - overrelaxation g -> g^omega (Mandula-Ogilvie) per subgroup, either to first order
- *    (a' = 1 - omega + omega*a, b' = omega*b, renormalised) or exactly.
- *  - Coulomb gauge: the temporal links are transformed with the spatial ones
- *    (Algorithm 1 applies g(x) "for all mu") but enter neither K nor F nor Delta.
- *  - reunitarisation (Section 3: every 20 steps) projects each link back to SU(3)
- *    by Gram-Schmidt on rows 0 and 1, row 2 = conj(row0 x row1); it is applied to the
- *    links the odd half-sweep has just written, which is every link when all sites
- *    are active.
+ *    previous ones (Section 1, sentence after Eq. (6), which prints only the SU(2)
+ *    solution and says to iterate over the subgroups for N > 2).
+ *  - overrelaxation g -> g^omega (Mandula-Ogilvie, cited after Eq. (6)) per subgroup,
+ *    either to first order (a' = 1 - omega + omega*a, b' = omega*b, renormalised; the
+ *    paper gives no formula, and this is the form that needs no trigonometry) or
+ *    exactly (the SU(2) power); both are the plain maximiser at omega = 1.
+ *  - Coulomb gauge: the temporal links are transformed with the spatial ones (Algorithm
+ *    1 applies g(x) to the links of every direction) but enter neither K nor F nor
+ *    Delta (the Coulomb condition involves the spatial directions only).
+ *  - reunitarisation (Section 3: every 20 steps; the method is not stated) projects each
+ *    link back to SU(3) by Gram-Schmidt on rows 0 and 1, row 2 = conj(row0 x row1); it
+ *    is applied to the links the odd half-sweep has just written, which is every link
+ *    when all sites are active.
  */
 #include <complex.h>
 #include <math.h>

@@ -298,7 +298,7 @@ struct gf_handle {
   double omega = 1.7, eps_switch = 1e-8;
   int form = GF_OR_FIRST_ORDER, reunit_interval = 20, check_interval = 1;
   int variant = GF_SWEEP_AUTO;
-  int polish = GF_POLISH_FP64;
+  int polish = GF_POLISH_SPLIT;
   int method = GF_METHOD_OR;
   double alpha = 0.08;
   void* kbuf = nullptr;

@@ -169,10 +169,29 @@ def ensemble_eps(seed: int, lo: float = 0.3, hi: float = 0.6) -> float:
     return float(_rng(seed, _PURPOSE_EPS).uniform(lo, hi))
 
 
-def ensemble(dims_list, seeds):
+def _ensemble_member(args):
+    d, s = args
+    return random_gauge_config(tuple(d), ensemble_eps(s), s)
+
+
+def ensemble(dims_list, seeds, workers: int | None = None):
     """One smooth-plus-random-gauge field per (dims, seed); eps ~ U[0.3, 0.6] is drawn
-    from each seed's own stream."""
-    return [random_gauge_config(tuple(d), ensemble_eps(s), s) for d, s in zip(dims_list, seeds)]
+    from each seed's own stream.
+
+    workers > 1 draws the members in that many processes (started with "spawn", so it is
+    safe after CUDA was initialised in the caller); every member depends only on its own
+    (dims, seed), so the fields are the same for any number of workers.  None uses one
+    worker per core, up to the number of members.
+    """
+    jobs = [(tuple(int(v) for v in d), int(s)) for d, s in zip(dims_list, seeds)]
+    if workers is None:
+        import os
+        workers = min(len(jobs), os.cpu_count() or 1)
+    if workers <= 1 or len(jobs) <= 1:
+        return [_ensemble_member(j) for j in jobs]
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_ensemble_member, jobs, chunksize=1)
 
 
 def to_host_layout(U: np.ndarray) -> np.ndarray:

@@ -68,3 +68,13 @@ def test_gauge_transform_keeps_invariants():
 def test_odd_extent_rejected():
     with pytest.raises(ValueError):
         fields.random_gauge_config((4, 4, 3, 4), 0.5, 1)
+
+
+def test_ensemble_is_the_same_for_any_number_of_workers():
+    # each member depends only on its own (dims, seed): the process pool changes nothing
+    dims_list = [(4, 4, 4, 4), (6, 4, 4, 2), (4, 4, 2, 6)]
+    seeds = [100, 101, 102]
+    a = fields.ensemble(dims_list, seeds, workers=1)
+    b = fields.ensemble(dims_list, seeds, workers=3)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    assert all(x.shape == (d[3], d[2], d[1], d[0], 4, 3, 3) for x, d in zip(a, dims_list))

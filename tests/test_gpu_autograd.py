@@ -25,9 +25,11 @@ def gf():
 
 
 def oracle_F_theta(U, c, gauge):
+    # g = exp(i c.lambda) by scipy's matrix exponential (batched over the sites)
+    from scipy.linalg import expm
     Lt, Lz, Ly, Lx = U.shape[:4]
     X = np.einsum("...a,aij->...ij", c.reshape(Lt, Lz, Ly, Lx, 8), fields.gell_mann())
-    W = fields.gauge_transform(U, fields.expi_hermitian(X, 1.0))
+    W = fields.gauge_transform(U, expm(1j * X))
     F, th, _, _ = oracle.measure(W, gauge)
     return F, th
 
@@ -120,7 +122,8 @@ def test_sgd_first_step_is_naive_descent_and_50_steps_ascend(gf):
         opt.step()
         if step == 0:
             D = oracle.delta(U).reshape(dims[::-1] + (3, 3))
-            W = fields.gauge_transform(U, fields.expi_hermitian(-0.5j * alpha * D, 1.0))
+            from scipy.linalg import expm
+            W = fields.gauge_transform(U, expm(0.5 * alpha * D))     # Eq. (7): g = exp(alpha/2 Delta)
             F1, th1 = oracle_F_theta(U, c.detach().cpu().numpy(), 0)
             assert abs(F1 - oracle.measure(W)[0]) < 1e-12
     F, th = functional_theta(c, fx)

@@ -64,38 +64,49 @@ def _verify_units(out, unit_theta, oracle_theta, eps):
     return int(done.sum())
 
 
+# The batched workloads run mixed FP32-12 -> double-float -> FP64 with the FP32 phase down
+# to theta = 1e-11 (the FP32 sweeps' floor is ~1e-13): every unit must reach theta < 1e-15
+# within the budget.  On these fields the sweeps a unit needs spread widely and theta is
+# not monotone under omega = 1.7 (the FP64 oracle shows both on the same fields); the
+# slowest units need ~70,000 (Coulomb slice) and ~87,000 (ensemble member) sweeps.
+UNITS_SWITCH = 1e-11
+
+
 def test_coulomb_32x3x64_mixed_per_slice(gf):
-    # Coulomb gauge 32^3 x 64, eps 0.5, seed 4: 64 slices fixed in one launch with
-    # per-slice theta and masks, FP32 bulk then double-float polish, stop at
-    # theta_t < 1e-15 per slice.  With omega = 1.7 the slowest slices of this field need
-    # far more sweeps than the others (the oracle shows the same spread on smaller
-    # slices), so the run has a fixed budget and every slice is checked by the oracle.
+    # Coulomb gauge 32^3 x 64, eps 0.5, seed 4: 64 slices fixed in one launch per half-sweep
+    # with per-slice theta and masks; stop at theta_t < 1e-15 on every slice
+    import time
     dims = (32, 32, 32, 64)
-    budget = 30000
+    budget = 120000
     U = fields.random_gauge_config(dims, 0.5, 4)
     fx = gf.GaugeFixer(dims, gf.GF_COULOMB, gf.GF_FP32_12, mixed=True)
-    gf.gf_set_polish(fx.h, gf.GF_POLISH_SPLIT)
+    gf.gf_set_mixed_switch(fx.h, UNITS_SWITCH)
     fx.upload(U)
+    t0 = time.perf_counter()
     out = fx.fix(1e-15, budget)
+    el = time.perf_counter() - t0
     _, _, _, uT = fx.functional_theta()
     got = fx.download()
     fx.close()
     F, th, F_t, th_t = oracle.measure(got, oracle.COULOMB)
     n = _verify_units(out, uT, th_t, 1e-15)
-    print(f"coulomb 32^3x64: {n}/64 slices below 1e-15 within {budget} sweeps; sweeps per slice "
-          f"min {out['iters'].min()} max {out['iters'].max()}, phases {out['phase_sweeps']}")
+    its = out["iters"]
+    print(f"coulomb 32^3x64: {n}/64 slices below 1e-15 in {el:.1f} s; sweeps per slice min {its.min()} "
+          f"median {int(np.median(its))} max {its.max()} (slice {int(np.argmax(its))}), "
+          f"phases {out['phase_sweeps']}")
+    assert n == 64 and out["rc"] == gf.GF_OK
 
 
 def test_ensemble_48_configs_one_batch(gf):
-    # 16 x 16^4 + 16 x 24^4 + 16 x 16^3x32, eps ~ U[0.3, 0.6], seeds 100..147, one batch,
-    # FP32 then double-float polish to theta < 1e-15 per configuration, fixed budget
+    # 16 x 16^4 + 16 x 24^4 + 16 x 16^3x32, eps ~ U[0.3, 0.6], seeds 100..147, one batch;
+    # every configuration to theta < 1e-15
     import time
     dims_list = [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 24)] * 16 + [(16, 16, 16, 32)] * 16
     seeds = list(range(100, 148))
-    budget = 20000
+    budget = 150000
     Us = fields.ensemble(dims_list, seeds)
     fb = gf.GaugeFixer(dims_list, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True)
-    gf.gf_set_polish(fb.h, gf.GF_POLISH_SPLIT)
+    gf.gf_set_mixed_switch(fb.h, UNITS_SWITCH)
     for i, U in enumerate(Us):
         fb.upload(U, i)
     torch.cuda.synchronize()
@@ -105,9 +116,12 @@ def test_ensemble_48_configs_one_batch(gf):
     _, _, _, uT = fb.functional_theta()
     th_o = np.array([oracle.measure(fb.download(i))[1] for i in range(48)])
     n = _verify_units(ob, uT, th_o, 1e-15)
-    unit_sweeps = int(ob["iters"].sum())
-    print(f"ensemble: {n}/48 below 1e-15; {unit_sweeps} unit-sweeps in {el:.2f} s = "
-          f"{unit_sweeps / el:.0f} unit-sweeps/s; phases {ob['phase_sweeps']}")
+    its = ob["iters"]
+    print(f"ensemble: {n}/48 below 1e-15 in {el:.1f} s; {int(its.sum())} unit-sweeps "
+          f"({its.sum() / el:.0f} per s); sweeps per member min {its.min()} median {int(np.median(its))} "
+          f"max {its.max()} (member {int(np.argmax(its))}), phases {ob['phase_sweeps']}")
+    print("ensemble sweeps per member:", its.tolist())
+    assert n == 48 and ob["rc"] == gf.GF_OK
     fb.close()
 
 
@@ -177,7 +191,8 @@ def test_autograd_32x4_gradient_and_sgd(gf):
         (-F).backward()
         opt.step()
         if step == 0:
-            W = fields.gauge_transform(U, fields.expi_hermitian(-0.5j * alpha * D.reshape(dims[::-1] + (3, 3)), 1.0))
+            from scipy.linalg import expm       # Eq. (7): g = exp(alpha/2 Delta), scipy's exponential
+            W = fields.gauge_transform(U, expm(0.5 * alpha * D.reshape(dims[::-1] + (3, 3))))
             F1, _ = functional_theta(c.detach(), fx)
             assert abs(F1.item() - oracle.measure(W)[0]) < 1e-12
     F, th = functional_theta(c.detach(), fx)

@@ -141,8 +141,24 @@ def test_100_sweeps_fp64(gf, gauge, repro):
         assert abs(out["theta"][0] - r["theta"]) <= 1e-12 * r["theta"]
     else:
         assert err < 1e-10, err
-        assert abs(out["F"][0] - r["F"]) <= 1e-12 * abs(r["F"])
-        assert abs(out["theta"][0] - r["theta"]) <= 1e-8 * r["theta"]
+        dF = abs(out["F"][0] - r["F"]) / abs(r["F"])
+        assert dF <= 1e-12, dF
+        # theta of Eq. (2) is a sum of squares of Delta(x), which is linear in the links.
+        # With every element of every link within eta of the oracle's (|re|, |im| <= eta),
+        # ||dU||_F <= 3 sqrt(2) eta, ||dDelta(x)||_F <= 2 * 2 nd * 3 sqrt(2) eta (A - A^+ over
+        # 2 nd links; the traceless projection does not increase the norm), so with
+        # theta_d = 96 nd^2 eta^2 >= sum_x ||dDelta||^2 / (3 V), Cauchy-Schwarz gives
+        # |dtheta| <= 2 sqrt(theta theta_d) + theta_d.  The rounding of the FMA kernels and
+        # of the oracle differ, so the two fields part by eta ~ 1e-12..1e-10 after 100
+        # sweeps, and theta is held to this bound at the observed eta (plus the
+        # measurement's own 1e-12).
+        nd = 4 if gauge == 0 else 3
+        th_d = 96 * nd * nd * err * err
+        bound = 2 * np.sqrt(r["theta"] * th_d) + th_d + 1e-12 * r["theta"]
+        dth = abs(out["theta"][0] - r["theta"])
+        print(f"FP64 FMA, 100 sweeps, gauge {gauge}: max link error {err:.2e}; F rel error {dF:.2e}; "
+              f"theta rel error {dth / r['theta']:.2e} (bound {bound / r['theta']:.2e}, theta {r['theta']:.3e})")
+        assert dth <= bound, (dth, bound)
     fx.close()
 
 

@@ -182,6 +182,7 @@ def test_fp32_8_mixed_reaches_1e15(gf):
     Vs = fa.download()
     fa.close()
     fx = gf.GaugeFixer(dims, gf.GF_LANDAU, gf.GF_FP32_8, mixed=True)
+    gf.gf_set_polish(fx.h, gf.GF_POLISH_FP64)
     fx.upload(U)
     out = fx.fix(1e-15, 3000)
     assert out["rc"] == gf.GF_OK

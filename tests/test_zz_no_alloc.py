@@ -2,14 +2,16 @@
 
 Callers that cannot allocate device memory (a pre-reserved pool, a loop that must not
 call cudaMalloc, a host process that owns every device allocation) pass only their
-field and an output buffer.  The call must give the values of the handle-based
-gf_functional_theta, within the FP64 tolerance used elsewhere (1e-12 relative), on
-two calls in a row (the shared static scratch keeps the previous call's contents).
-This file is collected last so a stop-at-first-failure run has run every other test.
+field and an output buffer.  The call must give the values of the CPU oracle's
+measurement (Eqs. (1)-(3)) and of the handle-based gf_functional_theta, within the FP64
+tolerance used elsewhere (1e-12 relative), on two calls in a row (the shared static
+scratch keeps the previous call's contents).  This file is collected last so a
+stop-at-first-failure run has run every other test.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1412_1498_gb300 import fields
 
 pytestmark = pytest.mark.gpu
@@ -32,12 +34,15 @@ def test_noalloc_matches_handle(gf, gauge, dims):
     fx.upload(U)
     F, th, _, _ = fx.functional_theta()
     fx.close()
+    rF, rth, _, _ = oracle.measure(U, gauge)
     Ud = torch.from_numpy(U).cuda()
     out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
     for _ in range(2):
         gf.gf_functional_theta_noalloc(dims, gauge, Ud.data_ptr(), out.data_ptr(), stream)
         got = out.cpu().numpy()
+        assert abs(got[0] - rF) <= 1e-12 * abs(rF), (got, rF)
+        assert abs(got[1] - rth) <= 1e-12 * rth, (got, rth)
         assert abs(got[0] - F[0]) <= 1e-12 * abs(F[0]), (got, F)
         assert abs(got[1] - th[0]) <= 1e-12 * th[0], (got, th)
         out.fill_(float("nan"))
