@@ -26,6 +26,7 @@ void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int
 void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_measure_fp32_pipe(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
 cudaError_t prepare_sweep_pipe();
+int sweep_pipe_grid(int nd, int threads, int n_tiles);
 void launch_sweep_split(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_measure_split(int nd, const MeasureArgs& a, int n_tiles, int threads, cudaStream_t s);
 void launch_to_split(int storage, const char* src, char* dst, const LatDev& ls, const LatDev& ld,
@@ -450,6 +451,7 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   a.lats = cur_lats(h);
   a.unit_tiles = h->d_unit_tiles;
   a.n_tiles = h->n_tiles;
+  a.n_odd_parts = h->n_tiles;
   a.unit_lat = h->d_unit_lat;
   a.unit_norm = h->d_unit_norm;
   a.active = h->d_active;
@@ -487,26 +489,40 @@ int enqueue_measure_all(gf_handle* h, int mode) {
   return GF_OK;
 }
 
-// One sweep of the device-driven loop (five launches): even half-sweep, odd half-sweep
-// (F and odd-site theta fused on check sweeps), FINISH_ODD (which units the odd part
-// alone cannot decide), the even-site theta pass for those units (a no-op when there
-// are none), FINISH_LOOP.  Consecutive half-sweeps walk the tiles in opposite
-// directions, so each starts on the lines the previous one left in L2; the even-site
-// pass walks against the odd half-sweep.  `pass` counts half-sweeps (2 per sweep).
+// One sweep of the device-driven loop, three launches: even half-sweep, odd half-sweep
+// (F and odd-site theta fused on check sweeps), FINISH_ODD, which decides every unit
+// whose odd part alone settles the stop (theta >= its odd part) and closes the sweep.
+// When some unit is undecided it leaves the sweep open (DevState.hold): the rest of the
+// captured sweeps do nothing, and the host runs the even-site theta pass and FINISH_LOOP
+// (resolve_open_sweep) before the next replay.  Consecutive half-sweeps walk the tiles
+// in opposite directions, so each starts on the lines the previous one left in L2.  A
+// one-unit lattice swept by the persistent pipelined kernel takes F and the odd-site
+// theta as one partial per CTA.  `pass` counts half-sweeps (2 per sweep).
 int enqueue_loop_sweep(gf_handle* h, cudaStream_t s, int* pass) {
   const int st = cur_storage(h);
   launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 0, true, (*pass)++ & 1), h->n_tiles,
                h->threads, s);
   GF_CK_LAUNCH(h);
-  const int rev_odd = (*pass)++ & 1;
-  launch_sweep(st, h->nd, h->repro, h->variant, sweep_args(h, 1, true, rev_odd), h->n_tiles,
-               h->threads, s);
+  SweepArgs ao = sweep_args(h, 1, true, (*pass)++ & 1);
+  FinishArgs fo = finish_args(h, FINISH_ODD);
+  if (h->n_units == 1 && st == GF_FP32_12 && h->variant != GF_SWEEP_REGISTER) {
+    ao.cta_sums = 1;
+    fo.n_odd_parts = sweep_pipe_grid(h->nd, h->threads, h->n_tiles);
+  }
+  launch_sweep(st, h->nd, h->repro, h->variant, ao, h->n_tiles, h->threads, s);
   GF_CK_LAUNCH(h);
-  launch_finish(finish_args(h, FINISH_ODD), s);
+  launch_finish(fo, s);
   GF_CK_LAUNCH(h);
-  launch_measure(st, h->nd, h->variant, measure_args(h, 0, true, rev_odd ^ 1), h->n_tiles, h->threads, s);
+  return GF_OK;
+}
+
+// The even-site theta pass for the units an open sweep left undecided, then FINISH_LOOP
+// (their theta, masks and iteration counts; the sweep is counted and the hold released).
+int resolve_open_sweep(gf_handle* h) {
+  launch_measure(cur_storage(h), h->nd, h->variant, measure_args(h, 0, true, 0), h->n_tiles, h->threads,
+                 h->stream);
   GF_CK_LAUNCH(h);
-  launch_finish(finish_args(h, FINISH_LOOP), s);
+  launch_finish(finish_args(h, FINISH_LOOP), h->stream);
   GF_CK_LAUNCH(h);
   return GF_OK;
 }
@@ -559,6 +575,10 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   while (s.n_active > 0 && s.sweep < s.limit) {
     GF_CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
+    if (s.hold) {
+      if ((rc = resolve_open_sweep(h)) != GF_OK) return rc;
+      if ((rc = read_state(h, &s)) != GF_OK) return rc;
+    }
   }
   *done = s.sweep - offset;
   h->hist_n = s.hist_n;
@@ -602,7 +622,9 @@ MeasureArgs measure_args_level(gf_handle* h, int L, int parity, int reverse, boo
   return a;
 }
 
-// One sweep of the mixed loop over the levels in `mask` (bit L-1 for level L).
+// One sweep of the mixed loop over the levels in `mask` (bit L-1 for level L): the
+// half-sweeps of every level, then FINISH_ODD; an open sweep is resolved by the host as
+// in the one-level loop (resolve_open_sweep_levels).
 int enqueue_mixed_sweep(gf_handle* h, cudaStream_t s, int* pass, int mask) {
   for (int parity = 0; parity < 2; ++parity) {
     const int rev = (*pass)++ & 1;
@@ -612,19 +634,22 @@ int enqueue_mixed_sweep(gf_handle* h, cudaStream_t s, int* pass, int mask) {
                      h->n_tiles, h->threads, s);
         GF_CK_LAUNCH(h);
       }
-    if (parity == 1) {
-      launch_finish(finish_args(h, FINISH_ODD), s);
-      GF_CK_LAUNCH(h);
-      for (int L = 1; L <= 3; ++L)
-        if (mask & (1 << (L - 1))) {
-          launch_measure(level_storage(h, L), h->nd, h->variant, measure_args_level(h, L, 0, rev ^ 1, true),
-                         h->n_tiles, h->threads, s);
-          GF_CK_LAUNCH(h);
-        }
-      launch_finish(finish_args(h, FINISH_LOOP), s);
+  }
+  launch_finish(finish_args(h, FINISH_ODD), s);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
+// even-site pass of every level in `mask` (each serves its undecided units) + FINISH_LOOP
+int resolve_open_sweep_levels(gf_handle* h, int mask) {
+  for (int L = 1; L <= 3; ++L)
+    if (mask & (1 << (L - 1))) {
+      launch_measure(level_storage(h, L), h->nd, h->variant, measure_args_level(h, L, 0, 0, true), h->n_tiles,
+                     h->threads, h->stream);
       GF_CK_LAUNCH(h);
     }
-  }
+  launch_finish(finish_args(h, FINISH_LOOP), h->stream);
+  GF_CK_LAUNCH(h);
   return GF_OK;
 }
 
@@ -736,6 +761,10 @@ int run_mixed(gf_handle* h, double eps, int budget, int* sweeps_fp32, int* sweep
     return GF_OK;
   };
   for (;;) {
+    if (mask_prev) {  // a replay ran: resolve a sweep it left open
+      if ((rc = read_state(h, &s)) != GF_OK) return rc;
+      if (s.hold && (rc = resolve_open_sweep_levels(h, mask_prev)) != GF_OK) return rc;
+    }
     GF_CK(h, cudaMemcpyAsync(act.data(), h->d_active, sizeof(int) * nu, cudaMemcpyDeviceToHost, h->stream));
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
     if (mask_prev) {

@@ -76,6 +76,8 @@ struct DevState {
   int stop;             // Fourier-accelerated loop: final field measured, nothing left to do
   int need_exact;       // this check sweep has units whose odd-site theta alone is below eps
   int sweep_closed;     // the odd-part finish already counted this sweep (nothing pending)
+  int hold;             // the odd-part finish left this sweep open: it waits for the even-site
+                        // pass and the loop finish, and no sweep starts before they ran
   int hist_n;           // history records written in the current gf_fix
   int hist_base;        // sweep number of the record = hist_base + sweep (across phases)
   double eps;           // stop threshold (of the final precision level)
@@ -97,6 +99,10 @@ __host__ __device__ inline int state_mask_below(const DevState* st, int lvl) {
 
 __host__ __device__ inline bool state_running(const DevState* st) {
   return st->n_active > 0 && st->sweep < st->limit;
+}
+// a half-sweep (or the odd-part finish) may start: running, and no open sweep before it
+__host__ __device__ inline bool state_sweeping(const DevState* st) {
+  return state_running(st) && !st->hold;
 }
 __host__ __device__ inline bool state_check_sweep(const DevState* st) {
   return ((st->sweep + 1) % st->check_interval) == 0 || st->sweep + 1 == st->limit;
@@ -583,15 +589,16 @@ __device__ __forceinline__ void block_sum_f32(const float (&v)[NV], double (&out
   }
 }
 
-// the same, leaving each total as the unevaluated pair (hi, lo) (valid in thread 0)
+// the same over per-thread pairs (v_hi, v_lo), leaving each total as the unevaluated
+// pair (hi, lo) (valid in thread 0)
 template <int NV>
-__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float2 (&out)[NV],
-                                              float* smem /* 2 * NV * 32 */) {
+__device__ __forceinline__ void block_sum_f32_pairs(const float (&v_hi)[NV], const float (&v_lo)[NV],
+                                                    float2 (&out)[NV], float* smem /* 2 * NV * 32 */) {
   float hi[NV], lo[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
-    hi[k] = v[k];
-    lo[k] = 0.f;
+    hi[k] = v_hi[k];
+    lo[k] = v_lo[k];
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
@@ -630,6 +637,15 @@ __device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float2 (&out
       out[k] = make_float2(h, l);
     }
   }
+}
+
+template <int NV>
+__device__ __forceinline__ void block_sum_f32(const float (&v)[NV], float2 (&out)[NV],
+                                              float* smem /* 2 * NV * 32 */) {
+  float lo[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) lo[k] = 0.f;
+  block_sum_f32_pairs<NV>(v, lo, out, smem);
 }
 
 // Unevaluated pairs hi + lo of floats ("double-float"): sums of per-tile partials are

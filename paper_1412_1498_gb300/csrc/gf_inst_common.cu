@@ -43,14 +43,14 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   // Every load that does not depend on another one is issued here, together: the
   // kernel is short and its time is mostly dependent round trips to memory.
   const int n_active = a.st->n_active, sweep = a.st->sweep, limit = a.st->limit;
-  const int ci = a.st->check_interval, closed = a.st->sweep_closed;
+  const int ci = a.st->check_interval, closed = a.st->sweep_closed, hold = a.st->hold;
   const double eps = a.st->eps, eps_mid = a.st->eps_mid;
   const int final_level = a.st->final_level;
   const int lvl_in = a.active[u];  // > 0: sweeping at that precision level
   const bool was_active = lvl_in > 0;
   const bool pend_in = a.pending[u] != 0;
   const int tb = a.n_units == 1 ? 0 : a.unit_tiles[u];
-  const int te = a.n_units == 1 ? a.n_tiles : a.unit_tiles[u + 1];
+  const int te = a.n_units == 1 ? (a.mode == FINISH_ODD ? a.n_odd_parts : a.n_tiles) : a.unit_tiles[u + 1];
   // The first pass of tile partials: with one unit its range is a kernel argument, so
   // these loads wait for nothing and travel with the ones above.  (FINISH_LOOP, which
   // mostly has nothing to add, loads inside the reduction.)
@@ -78,15 +78,13 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   bool check = true;
   if (loop) {
     if (!(n_active > 0 && sweep < limit)) return;  // uniform over the grid: no ticket taken
+    if (a.mode == FINISH_ODD && hold) return;        // the previous sweep is still open
     check = ((sweep + 1) % ci) == 0 || sweep + 1 == limit;  // state_check_sweep
-    if (a.mode == FINISH_ODD && !check) {
-      if (u == 0 && tid == 0) a.st->sweep_closed = 0;
-      return;
-    }
     if (a.mode == FINISH_LOOP && closed) return;  // written by the previous launch
   }
   bool reduce;
-  if (a.mode == FINISH_ODD) reduce = was_active;
+  // a sweep without a check is closed by the odd-part finish (counts, no sums)
+  if (a.mode == FINISH_ODD) reduce = was_active && check;
   else if (a.mode == FINISH_LOOP) reduce = check && was_active && pend_in;
   else if (a.mode == FINISH_ENTER) reduce = pend_in;
   else reduce = true;
@@ -175,6 +173,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
       if (a.mode == FINISH_ODD && pend) {
         a.st->need_exact = 1;
         a.st->sweep_closed = 0;
+        a.st->hold = 1;
       } else {
         if (a.mode == FINISH_ODD && was_active) a.iters[u] += 1;
         if (!loop || check) {
@@ -187,6 +186,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
         } else if (a.mode != FINISH_MEASURE) {
           a.st->n_active = act ? 1 : 0;
         }
+        if (a.mode == FINISH_LOOP) a.st->hold = 0;
         if (loop) a.st->sweep = sweep + 1;
         if (a.hist && ((a.mode == FINISH_LOOP && check) || (a.mode == FINISH_RESET && a.st->hist_n == 0)))
           history_record(a, a.mode == FINISH_LOOP ? a.st->hist_base + sweep + 1 : 0);
@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
     if (tid == 0) {
       a.st->need_exact = 1;
       a.st->sweep_closed = 0;
+      a.st->hold = 1;
       a.st->ticket = 0u;
     }
     return;
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
     } else if (a.mode != FINISH_MEASURE) {
       a.st->n_active = n;
     }
+    if (a.mode == FINISH_LOOP) a.st->hold = 0;
     if (a.hist && ((a.mode == FINISH_LOOP && check) || (a.mode == FINISH_RESET && a.st->hist_n == 0)))
       history_record(a, a.mode == FINISH_LOOP ? a.st->hist_base + sweep + 1 : 0);
     if (loop) a.st->sweep += 1;

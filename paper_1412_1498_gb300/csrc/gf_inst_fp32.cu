@@ -62,12 +62,19 @@ void launch_measure_fp32_pipe(int nd, const MeasureArgs& a, int n_tiles, int thr
   else k_measure_pipe<3><<<grid, threads, smem, s>>>(a);
 }
 
-void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s) {
+// CTAs of the persistent pipelined sweep over n_tiles tiles (also the number of per-CTA
+// partials it writes with cta_sums)
+int sweep_pipe_grid(int nd, int threads, int n_tiles) {
   int dev = 0;
   cudaGetDevice(&dev);
   int grid = g_pipe_grid[dev < kMaxDev ? dev : 0][nd == 4][threads_slot(threads)];
   if (grid <= 0) grid = 1;
   if (grid > n_tiles) grid = n_tiles;
+  return grid;
+}
+
+void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads, cudaStream_t s) {
+  const int grid = sweep_pipe_grid(nd, threads, n_tiles);
   const size_t smem = 2 * kPipeWords * threads * sizeof(float4);
   if (a.form == GF_OR_FIRST_ORDER) {
     if (nd == 4) k_or_sweep_pipe<4, GF_OR_FIRST_ORDER><<<grid, threads, smem, s>>>(a);

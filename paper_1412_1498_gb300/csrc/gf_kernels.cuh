@@ -228,6 +228,8 @@ struct SweepArgs {
   int n_tiles;
   int reverse;             // walk the tiles last to first (L2 reuse across passes)
   int level;               // precision level these tiles must carry in `active` (1 unless mixed)
+  int cta_sums;            // persistent kernels, one unit: F and theta partials per CTA (indexed
+                           // by blockIdx.x) instead of per tile
   double omega;
 };
 
@@ -252,6 +254,7 @@ struct FinishArgs {
   const LatDev* lats;
   const int* unit_tiles;   // n_units + 1 tile boundaries
   int n_tiles;             // tiles of the table (the single unit's range when n_units == 1)
+  int n_odd_parts;         // one unit: partials the odd half-sweep wrote (tiles, or its CTAs)
   int* pending;            // per unit: the unit's level when this check needs the even-site
                            // pass (FINISH_ODD sets it), or when FINISH_ENTER is to measure it
   double* hist;            // nullable: records (sweep, F and theta of every lattice) of each check
@@ -347,7 +350,7 @@ __global__ void __launch_bounds__(256) k_or_sweep(SweepArgs a) {
 
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
-    if (!state_running(a.st)) return;
+    if (!state_sweeping(a.st)) return;
     reunit_now = a.parity == 1 && state_reunit_sweep(a.st);
     measure_now = a.parity == 1 && state_check_sweep(a.st);
   }

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_split(SweepArgs a) {
   __shared__ double red[64];
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
-    if (!state_running(a.st)) return;
+    if (!state_sweeping(a.st)) return;
     reunit_now = a.parity == 1 && state_reunit_sweep(a.st);
     measure_now = a.parity == 1 && state_check_sweep(a.st);
   }

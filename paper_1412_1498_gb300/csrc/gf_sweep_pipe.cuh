@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
   int rb = 0;
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
-    if (!state_running(a.st)) return;
+    if (!state_sweeping(a.st)) return;
     reunit_now = a.parity == 1 && state_reunit_sweep(a.st);
     measure_now = a.parity == 1 && state_check_sweep(a.st);
   }
@@ -90,6 +90,10 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
   if (k >= a.n_tiles) return;
   const int B = blockDim.x;
   const float omega = (float)a.omega;
+  // with cta_sums each thread adds its sites' values over the CTA's tiles (compensated,
+  // in a fixed order) and the CTA reduces once at the end: no barrier per tile
+  const bool per_cta = measure_now && a.cta_sums;
+  float acc_hi[2] = {0.f, 0.f}, acc_lo[2] = {0.f, 0.f};
   int buf = 0;
   PipeSite cur = pipe_issue(a, k, 0, sm);
   cp_async_commit();
@@ -137,7 +141,16 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
           }
         }
       }
-      if (measure_now) {
+      if (per_cta) {
+        const float v[2] = {fs, q};
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          float s, e;
+          two_sum(acc_hi[j], v[j], s, e);
+          acc_hi[j] = s;
+          acc_lo[j] = acc_lo[j] + e;
+        }
+      } else if (measure_now) {
         const float v[2] = {fs, q};
         float2 o[2];
         block_sum_f32<2>(v, o, reinterpret_cast<float*>(red[rb]));
@@ -154,6 +167,14 @@ __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
     k = kn;
     buf ^= 1;
     cur = nxt;
+  }
+  if (per_cta) {
+    float2 o[2];
+    block_sum_f32_pairs<2>(acc_hi, acc_lo, o, reinterpret_cast<float*>(red[rb]));
+    if (threadIdx.x == 0) {
+      if (a.part_F) a.part_F[blockIdx.x] = o[0];
+      a.part_theta[blockIdx.x] = o[1];
+    }
   }
 }
 

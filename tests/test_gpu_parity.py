@@ -148,10 +148,10 @@ def test_100_sweeps_fp64(gf, gauge, repro):
         # ||dU||_F <= 3 sqrt(2) eta, ||dDelta(x)||_F <= 2 * 2 nd * 3 sqrt(2) eta (A - A^+ over
         # 2 nd links; the traceless projection does not increase the norm), so with
         # theta_d = 96 nd^2 eta^2 >= sum_x ||dDelta||^2 / (3 V), Cauchy-Schwarz gives
-        # |dtheta| <= 2 sqrt(theta theta_d) + theta_d.  The rounding of the FMA kernels and
-        # of the oracle differ, so the two fields part by eta ~ 1e-12..1e-10 after 100
-        # sweeps, and theta is held to this bound at the observed eta (plus the
-        # measurement's own 1e-12).
+        # |dtheta| <= 2 sqrt(theta theta_d) + theta_d.  The FMA kernels round differently
+        # from the oracle and the fields part by eta ~ 1e-14 after 100 sweeps here, which
+        # bounds theta's relative error by ~1e-10; the error met is ~1e-14, inside the
+        # 1e-12 asked of F and theta.
         nd = 4 if gauge == 0 else 3
         th_d = 96 * nd * nd * err * err
         bound = 2 * np.sqrt(r["theta"] * th_d) + th_d + 1e-12 * r["theta"]
@@ -159,6 +159,7 @@ def test_100_sweeps_fp64(gf, gauge, repro):
         print(f"FP64 FMA, 100 sweeps, gauge {gauge}: max link error {err:.2e}; F rel error {dF:.2e}; "
               f"theta rel error {dth / r['theta']:.2e} (bound {bound / r['theta']:.2e}, theta {r['theta']:.3e})")
         assert dth <= bound, (dth, bound)
+        assert dth <= 1e-12 * r["theta"], dth / r["theta"]
     fx.close()
 
 
@@ -369,7 +370,10 @@ def test_block_sizes_agree(gf, threads):
 def test_pipelined_sweep_equals_register_sweep(gf, gauge, threads):
     # the shared-memory pipelined FP32-12 kernels (sweep and F/theta pass) do the register
     # kernels' arithmetic in the same order: same bits, with reunitarisation, checks and
-    # Coulomb masks
+    # Coulomb masks.  With one unit (Landau) the persistent kernel adds F and the odd-site
+    # theta per CTA instead of per tile, so the in-loop sums are rounded in another order
+    # (compensated FP32 pairs, ~1e-14 relative); the per-tile sums of the Coulomb slices
+    # and of the measurement pass keep every bit.
     dims = DIMS if gauge == 0 else DIMS_C
     U = fields.random_gauge_config(dims, 0.5, 72)
     outs = []
@@ -385,7 +389,12 @@ def test_pipelined_sweep_equals_register_sweep(gf, gauge, threads):
         fx.close()
     a, b = outs
     assert np.array_equal(a[0], b[0])
-    assert a[1:3] == b[1:3] and np.array_equal(a[3], b[3]) and a[4] == b[4]
+    assert np.array_equal(a[3], b[3])
+    if gauge == 1:
+        assert a[1:3] == b[1:3] and a[4] == b[4]
+    else:
+        for x, y in ((a[1], b[1]), (a[2], b[2]), (a[4], b[4])):
+            assert abs(x - y) <= 1e-12 * abs(x), (x, y)
     assert all(np.array_equal(x, y) for x, y in zip(a[5], b[5]))
 
 
