@@ -312,7 +312,7 @@ def units_leg(gf, dev, stream, peak: float, n_coulomb: int = 400, n_ensemble: in
         "time_to_theta_1e-15": to_theta([dims], gf.GF_COULOMB, Uc, t, v)}
     del Uc
     dims_list = [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 24)] * 16 + [(16, 16, 16, 32)] * 16
-    Us = fields.ensemble(dims_list, list(range(100, 148)))
+    Us = fields.ensemble(dims_list, list(range(100, 148)), workers=min(16, os.cpu_count() or 1))
     ms, t, v = throughput(dims_list, gf.GF_LANDAU, Us, n_ensemble)
     vtot = sum(d[0] * d[1] * d[2] * d[3] for d in dims_list)
     gbps = 16 * vtot * LINK_B / (ms * 1e-3) / 1e9

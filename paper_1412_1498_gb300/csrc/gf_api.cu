@@ -489,13 +489,17 @@ int enqueue_measure_all(gf_handle* h, int mode) {
   return GF_OK;
 }
 
-// One sweep of the device-driven loop, three launches: even half-sweep, odd half-sweep
-// (F and odd-site theta fused on check sweeps), FINISH_ODD, which decides every unit
-// whose odd part alone settles the stop (theta >= its odd part) and closes the sweep.
-// When some unit is undecided it leaves the sweep open (DevState.hold): the rest of the
-// captured sweeps do nothing, and the host runs the even-site theta pass and FINISH_LOOP
-// (resolve_open_sweep) before the next replay.  Consecutive half-sweeps walk the tiles
-// in opposite directions, so each starts on the lines the previous one left in L2.  A
+// One sweep of the device-driven loop: even half-sweep, odd half-sweep (F and odd-site
+// theta fused on check sweeps), FINISH_ODD, which decides every unit whose odd part alone
+// settles the stop (theta >= its odd part) and closes the sweep.  When some unit is
+// undecided it leaves the sweep open (DevState.hold) for the even-site theta pass and
+// FINISH_LOOP.  With one unit that happens on the last sweeps of a run only, so those
+// two are not captured: the rest of the replay does nothing and the host runs them
+// (resolve_open_sweep) before the next replay, and a sweep is three launches.  With many
+// units some unit is undecided on many sweeps (theta is not monotone and units hover
+// about their thresholds), so they are captured after FINISH_ODD and run (as no-ops when
+// nothing is pending) on every sweep.  Consecutive half-sweeps walk the tiles in
+// opposite directions, so each starts on the lines the previous one left in L2.  A
 // one-unit lattice swept by the persistent pipelined kernel takes F and the odd-site
 // theta as one partial per CTA.  `pass` counts half-sweeps (2 per sweep).
 int enqueue_loop_sweep(gf_handle* h, cudaStream_t s, int* pass) {
@@ -513,6 +517,12 @@ int enqueue_loop_sweep(gf_handle* h, cudaStream_t s, int* pass) {
   GF_CK_LAUNCH(h);
   launch_finish(fo, s);
   GF_CK_LAUNCH(h);
+  if (h->n_units > 1) {
+    launch_measure(st, h->nd, h->variant, measure_args(h, 0, true, ao.reverse ^ 1), h->n_tiles, h->threads, s);
+    GF_CK_LAUNCH(h);
+    launch_finish(finish_args(h, FINISH_LOOP), s);
+    GF_CK_LAUNCH(h);
+  }
   return GF_OK;
 }
 
@@ -623,11 +633,13 @@ MeasureArgs measure_args_level(gf_handle* h, int L, int parity, int reverse, boo
 }
 
 // One sweep of the mixed loop over the levels in `mask` (bit L-1 for level L): the
-// half-sweeps of every level, then FINISH_ODD; an open sweep is resolved by the host as
-// in the one-level loop (resolve_open_sweep_levels).
+// half-sweeps of every level, then FINISH_ODD; as in the one-level loop, the even-site
+// pass of every level and FINISH_LOOP follow in the graph when there are many units,
+// and an open sweep of one unit is resolved by the host (resolve_open_sweep_levels).
 int enqueue_mixed_sweep(gf_handle* h, cudaStream_t s, int* pass, int mask) {
+  int rev = 0;
   for (int parity = 0; parity < 2; ++parity) {
-    const int rev = (*pass)++ & 1;
+    rev = (*pass)++ & 1;
     for (int L = 1; L <= 3; ++L)
       if (mask & (1 << (L - 1))) {
         launch_sweep(level_storage(h, L), h->nd, h->repro, h->variant, sweep_args_level(h, L, parity, rev),
@@ -637,6 +649,16 @@ int enqueue_mixed_sweep(gf_handle* h, cudaStream_t s, int* pass, int mask) {
   }
   launch_finish(finish_args(h, FINISH_ODD), s);
   GF_CK_LAUNCH(h);
+  if (h->n_units > 1) {
+    for (int L = 1; L <= 3; ++L)
+      if (mask & (1 << (L - 1))) {
+        launch_measure(level_storage(h, L), h->nd, h->variant, measure_args_level(h, L, 0, rev ^ 1, true),
+                       h->n_tiles, h->threads, s);
+        GF_CK_LAUNCH(h);
+      }
+    launch_finish(finish_args(h, FINISH_LOOP), s);
+    GF_CK_LAUNCH(h);
+  }
   return GF_OK;
 }
 

@@ -174,19 +174,17 @@ def _ensemble_member(args):
     return random_gauge_config(tuple(d), ensemble_eps(s), s)
 
 
-def ensemble(dims_list, seeds, workers: int | None = None):
+def ensemble(dims_list, seeds, workers: int = 1):
     """One smooth-plus-random-gauge field per (dims, seed); eps ~ U[0.3, 0.6] is drawn
     from each seed's own stream.
 
     workers > 1 draws the members in that many processes (started with "spawn", so it is
     safe after CUDA was initialised in the caller); every member depends only on its own
-    (dims, seed), so the fields are the same for any number of workers.  None uses one
-    worker per core, up to the number of members.
+    (dims, seed), so the fields are the same for any number of workers.  A spawned worker
+    imports the caller's main module, so a script that asks for workers must keep its
+    top-level work under an ``if __name__ == "__main__":`` guard.
     """
     jobs = [(tuple(int(v) for v in d), int(s)) for d, s in zip(dims_list, seeds)]
-    if workers is None:
-        import os
-        workers = min(len(jobs), os.cpu_count() or 1)
     if workers <= 1 or len(jobs) <= 1:
         return [_ensemble_member(j) for j in jobs]
     import multiprocessing as mp

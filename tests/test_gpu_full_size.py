@@ -104,7 +104,8 @@ def test_ensemble_48_configs_one_batch(gf):
     dims_list = [(16, 16, 16, 16)] * 16 + [(24, 24, 24, 24)] * 16 + [(16, 16, 16, 32)] * 16
     seeds = list(range(100, 148))
     budget = 150000
-    Us = fields.ensemble(dims_list, seeds)
+    import os
+    Us = fields.ensemble(dims_list, seeds, workers=min(16, os.cpu_count() or 1))
     fb = gf.GaugeFixer(dims_list, gf.GF_LANDAU, gf.GF_FP32_12, mixed=True)
     gf.gf_set_mixed_switch(fb.h, UNITS_SWITCH)
     for i, U in enumerate(Us):
