@@ -492,10 +492,10 @@ def run_gpu(args):
         q1.record(stream)
         q1.synchronize()
         ms_it = q0.elapsed_time(q1) / args.fasd_iters
-        # HBM bytes an iteration must move: links read for Delta (4 V b) and read and
-        # written in the update (8 V b), g written and read once (2 x 48 V B), k-space
-        # (4 complex FP32 fields, 32 V B) written and read back once; the z/t transform
-        # works on L2-resident k-space
+        # bytes an iteration moves: links read for Delta (4 V b) and read and written in
+        # the update (8 V b), k-space (4 complex FP32 fields, 32 V B) written by the Delta
+        # pass and read back once, g (rows 0, 1: 48 V B) written by the inverse transform
+        # and read once by the update; the z/t transform works on L2-resident k-space
         fasd_bytes = 12 * V * LINK_B + 2 * 48 * V + 2 * 32 * V
         fasd = {"iterations": args.fasd_iters, "ms_per_iteration": ms_it,
                 "algorithmic_GBps": fasd_bytes / (ms_it * 1e-3) / 1e9, "bytes_per_iteration": fasd_bytes,

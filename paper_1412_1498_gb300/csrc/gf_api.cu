@@ -42,7 +42,6 @@ void launch_fasd_finish(const FasdArgs& a, cudaStream_t s);
 void launch_fasd_zt(int storage, int nd, const FasdArgs& a, cudaStream_t s);
 void launch_fasd_xy_inv_g(int storage, int nd, const FasdArgs& a, cudaStream_t s);
 void launch_fasd_update(int storage, int nd, const FasdArgs& a, cudaStream_t s);
-void launch_fasd_bump(const FasdArgs& a, cudaStream_t s);
 size_t ad_partial_doubles(long long V);
 void launch_ad_forward(const AdArgs& a, cudaStream_t s);
 void launch_ad_backward(const AdArgs& a, cudaStream_t s);
@@ -874,7 +873,7 @@ FasdArgs fasd_args(gf_handle* h, bool loop, int mode) {
   return a;
 }
 
-// One iteration: Delta + F/theta (A, B), then, while running, C, D, E, F.
+// One iteration: Delta + F/theta (A, B), then, while running, C, D, E (E counts it).
 int enqueue_fasd_iteration(gf_handle* h, cudaStream_t s) {
   const FasdArgs a = fasd_args(h, true, FINISH_LOOP);
   launch_fasd_delta_xy(h->storage, h->nd, a, s);
@@ -886,8 +885,6 @@ int enqueue_fasd_iteration(gf_handle* h, cudaStream_t s) {
   launch_fasd_xy_inv_g(h->storage, h->nd, a, s);
   GF_CK_LAUNCH(h);
   launch_fasd_update(h->storage, h->nd, a, s);
-  GF_CK_LAUNCH(h);
-  launch_fasd_bump(a, s);
   GF_CK_LAUNCH(h);
   return GF_OK;
 }

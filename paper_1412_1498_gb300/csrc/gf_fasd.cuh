@@ -7,9 +7,12 @@
 //   C  k_fasd_zt         per (kx, ky): forward FFT along z (and t for Landau), the filter
 //                        (alpha/2) p^2_max / p^2 / N (k = 0 mode set to 0), inverse FFT;
 //   D  k_fasd_xy_inv_g   per (z,t) plane: inverse FFT along y, x, then
-//                        g(x) = reunit(1 + Delta~(x)) (first-order exponential, Sec. 1);
-//   E  k_fasd_update     per site: U_mu(x) <- g(x) U_mu(x) g(x+mu)^+ for every mu;
-//   F  k_fasd_bump       iteration counters.
+//                        g(x) = reunit(1 + Delta~(x)) (first-order exponential, Sec. 1),
+//                        rows 0 and 1 stored in lexicographic site order;
+//   E  k_fasd_update     per site, in lexicographic order: U_mu(x) <- g(x) U_mu(x)
+//                        g(x+mu)^+ for every mu (the g of a block's forward neighbours lie
+//                        in its own and the next planes, just written: L2 hits); its last
+//                        block counts the iteration.
 //
 // Delta is anti-Hermitian and traceless and the filter is real and even in k, so the
 // filtered field stays anti-Hermitian: only four complex fields are transformed -- the
@@ -21,7 +24,9 @@
 
 namespace gf {
 
-
+// threads of the plane kernels (A, D): one x- or y-line of the four fields per thread
+// (4 x 32 lines at 32^2 planes), four blocks per SM
+constexpr int kFasdThreads = 128;
 
 // ------------------------------------------------------------------------- FFT
 // In-place radix-2 FFTs of n_lines lines of length L = 2^logL in shared memory; line l
@@ -214,26 +219,41 @@ __device__ __forceinline__ bool fasd_running(const DevState* st) {
   return st == nullptr || (st->n_active > 0 && st->sweep < st->limit);
 }
 
-// g rows 0, 1 in the links' precision: FP32 as 3 float4 words, FP64 as 6 double2 words
+// g = reunit(1 + Delta~) from the four transformed fields Delta~_01, Delta~_02,
+// Delta~_12 and (Im Delta~_00, Im Delta~_11): Delta~ is anti-Hermitian and traceless, so
+// the rest follows.
 template <class T>
-__device__ __forceinline__ void g_store(char* gbuf, long long V, int idx, const cx<T> (&g)[9]) {
+__device__ __forceinline__ void g_from_delta(cx<T> d01, cx<T> d02, cx<T> d12, cx<T> dd, cx<T> (&g)[9]) {
+  g[0] = {T(1), dd.re};
+  g[4] = {T(1), dd.im};
+  g[8] = {T(1), -(dd.re + dd.im)};
+  g[1] = d01; g[2] = d02; g[5] = d12;
+  g[3] = cneg(cconj(d01)); g[6] = cneg(cconj(d02)); g[7] = cneg(cconj(d12));
+  reunit(g);
+}
+
+// g rows 0, 1 in the links' precision, site `at` (lexicographic): FP32 as 3 float4
+// words, FP64 as 6 double2 words, each word a plane of V entries
+template <class T>
+__device__ __forceinline__ void g_store(char* gbuf, long long V, long long at, const cx<T> (&g)[9]) {
   if constexpr (sizeof(T) == 4) {
     float4* p = reinterpret_cast<float4*>(gbuf);
 #pragma unroll
-    for (int w = 0; w < 3; ++w) p[w * V + idx] = make_float4(g[2 * w].re, g[2 * w].im, g[2 * w + 1].re, g[2 * w + 1].im);
+    for (int w = 0; w < 3; ++w) p[w * V + at] = make_float4(g[2 * w].re, g[2 * w].im, g[2 * w + 1].re, g[2 * w + 1].im);
   } else {
     double2* p = reinterpret_cast<double2*>(gbuf);
 #pragma unroll
-    for (int w = 0; w < 6; ++w) p[w * V + idx] = make_double2(g[w].re, g[w].im);
+    for (int w = 0; w < 6; ++w) p[w * V + at] = make_double2(g[w].re, g[w].im);
   }
 }
-template <class T>
-__device__ __forceinline__ void g_load(const char* gbuf, long long V, int idx, cx<T> (&g)[9]) {
+// rows 0, 1 (and row 2 = conj(row0 x row1) when full)
+template <class T, bool FULL>
+__device__ __forceinline__ void g_load(const char* gbuf, long long V, long long at, cx<T> (&g)[9]) {
   if constexpr (sizeof(T) == 4) {
     const float4* p = reinterpret_cast<const float4*>(gbuf);
 #pragma unroll
     for (int w = 0; w < 3; ++w) {
-      const float4 v = p[w * V + idx];
+      const float4 v = p[w * V + at];
       g[2 * w].re = v.x;
       g[2 * w].im = v.y;
       g[2 * w + 1].re = v.z;
@@ -243,17 +263,17 @@ __device__ __forceinline__ void g_load(const char* gbuf, long long V, int idx, c
     const double2* p = reinterpret_cast<const double2*>(gbuf);
 #pragma unroll
     for (int w = 0; w < 6; ++w) {
-      const double2 v = p[w * V + idx];
+      const double2 v = p[w * V + at];
       g[w].re = v.x;
       g[w].im = v.y;
     }
   }
-  third_row(g, g + 6);
+  if constexpr (FULL) third_row(g, g + 6);
 }
 
 // ------------------------------------------------------------------------- A: Delta + FFT xy
 template <int S, int ND>
-__global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_delta_xy(FasdArgs a) {
+__global__ void __launch_bounds__(kFasdThreads, S == GF_FP64_18 ? 2 : 4) k_fasd_delta_xy(FasdArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   constexpr int NE = St::NE;
@@ -543,7 +563,7 @@ __global__ void __launch_bounds__(256, 2) k_fasd_zt(FasdArgs a) {
 
 // ------------------------------------------------------------------------- D: inverse xy, g
 template <int S, int ND>
-__global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_xy_inv_g(FasdArgs a) {
+__global__ void __launch_bounds__(kFasdThreads, S == GF_FP64_18 ? 2 : 4) k_fasd_xy_inv_g(FasdArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -569,23 +589,17 @@ __global__ void __launch_bounds__(256, S == GF_FP64_18 ? 1 : 2) k_fasd_xy_inv_g(
   fft_lines_reg(pl, twx, 4 * Ly, a.logL[0], 1, 0, pitch, 1, +1);
   for (int i = threadIdx.x; i < P; i += blockDim.x) {
     const int x = i & (Lx - 1), y = i >> a.logL[0];
-    const long long lexi = x + (long long)Lx * (y + (long long)Ly * (z + (long long)lat.L[2] * t));
-    const int idx = ((x + y + z + t) & 1) * lat.Vh + (int)(lexi >> 1);
     // Delta~ (already scaled by alpha/2 p^2_max/p^2/N): anti-Hermitian, traceless
     const int r = y * pitch + x, fs = Ly * pitch;
-    const cx<T> d01 = pl[r], d02 = pl[fs + r], d12 = pl[2 * fs + r], dd = pl[3 * fs + r];
     cx<T> g[9];
-    g[0] = {T(1), dd.re};
-    g[4] = {T(1), dd.im};
-    g[8] = {T(1), -(dd.re + dd.im)};
-    g[1] = d01; g[2] = d02; g[5] = d12;
-    g[3] = cneg(cconj(d01)); g[6] = cneg(cconj(d02)); g[7] = cneg(cconj(d12));
-    reunit(g);
-    g_store<T>(a.gbuf, lat.V, idx, g);
+    g_from_delta<T>(pl[r], pl[fs + r], pl[2 * fs + r], pl[3 * fs + r], g);
+    g_store<T>(a.gbuf, lat.V, plane0 + i, g);
   }
 }
 
 // ------------------------------------------------------------------------- E: update
+// One site per thread in lexicographic order, so a block's forward neighbours lie in its
+// own and the next planes, whose g the previous kernel has just written (L2 hits).
 template <int S, int ND>
 __global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
   using St = Store<S>;
@@ -595,11 +609,16 @@ __global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
   const LatDev& lat = a.lat;
   const bool reunit_now = a.st ? state_reunit_sweep(a.st) : a.reunit != 0;
   char* base = a.links + lat.off_bytes;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < lat.V;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int p = i >= lat.Vh ? 1 : 0;
-    const int h = (int)(i - (long long)p * lat.Vh);
-    const Site s = site_of(lat, p, h);
+  const long long s0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (s0 < lat.V) {
+    Site s;
+    s.lexi = s0;
+    s.x = (int)(s0 & (lat.L[0] - 1));                        // Lx, Ly, Lz are powers of 2
+    s.y = (int)((s0 >> a.logL[0]) & (lat.L[1] - 1));
+    s.z = (int)((s0 >> (a.logL[0] + a.logL[1])) & (lat.L[2] - 1));
+    s.t = (int)(s0 >> (a.logL[0] + a.logL[1] + a.logL[2]));
+    const int p = (s.x + s.y + s.z + s.t) & 1;
+    const int idx = p * lat.Vh + (int)(s0 >> 1);
     // Coulomb gauge with per-slice masks: g = 1 on the sites of a converged slice, so its
     // spatial links stay as they are while a temporal link into an active slice still
     // takes that slice's g(x + t)^+ on the right
@@ -607,34 +626,39 @@ __global__ void __launch_bounds__(128) k_fasd_update(FasdArgs a) {
     if (ND == 3 && a.active) {
       act = a.active[s.t] != 0;
       act_next = a.active[s.t == lat.L[3] - 1 ? 0 : s.t + 1] != 0;
-      if (!act && !act_next) continue;
     }
-    cx<T> g[9];
-    if (act) g_load<T>(a.gbuf, lat.V, (int)i, g);
+    if (act || act_next) {
+      cx<T> g[9];
+      if (act) g_load<T, NE == 9>(a.gbuf, lat.V, s0, g);  // left_mul of 12-real links reads rows 0, 1
 #pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-      const bool act_fwd = mu == 3 ? act_next : act;
-      if (!act && !act_fwd) continue;
-      cx<T> u[NE], gn[9];
-      St::load(base, lat.V, mu, (int)i, u);
-      if (act) left_mul(g, u);
-      if (act_fwd) {
-        g_load<T>(a.gbuf, lat.V, (1 - p) * lat.Vh + (int)(fwd_lexi(lat, s, mu) >> 1), gn);
-        right_mul_dag(u, gn);
+      for (int mu = 0; mu < 4; ++mu) {
+        const bool act_fwd = mu == 3 ? act_next : act;
+        if (!act && !act_fwd) continue;
+        cx<T> u[NE], gn[9];
+        St::load(base, lat.V, mu, idx, u);
+        if (act) left_mul(g, u);
+        if (act_fwd) {
+          g_load<T, true>(a.gbuf, lat.V, fwd_lexi(lat, s, mu), gn);
+          right_mul_dag(u, gn);
+        }
+        if (reunit_now) reunit(u);
+        St::store(base, lat.V, mu, idx, u);
       }
-      if (reunit_now) reunit(u);
-      St::store(base, lat.V, mu, (int)i, u);
     }
   }
-}
-
-// ------------------------------------------------------------------------- F: counters
-__global__ void k_fasd_bump(FasdArgs a) {
-  if (a.st == nullptr || a.active == nullptr || !fasd_running(a.st)) return;
+  // the last block counts the iteration (every block read the state before any count)
+  if (a.st == nullptr || a.active == nullptr) return;
+  __shared__ bool s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.st->ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
   for (int u = threadIdx.x; u < a.n_units; u += blockDim.x)
     if (a.active[u]) a.iters[u] += 1;
-  __syncthreads();
-  if (threadIdx.x == 0) a.st->sweep += 1;
+  if (threadIdx.x == 0) {
+    a.st->ticket = 0u;
+    a.st->sweep += 1;
+  }
 }
 
 }  // namespace gf

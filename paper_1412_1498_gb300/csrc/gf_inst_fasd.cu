@@ -39,7 +39,7 @@ cudaError_t prepare_fasd(int storage, int nd, const LatDev& lat) {
 void launch_fasd_delta_xy(int storage, int nd, const FasdArgs& a, cudaStream_t s) {
   const dim3 grid(a.lat.L[2], a.lat.L[3]);
   const size_t sm = plane_smem(storage, a.lat);
-#define GF_CALL(S, T, ND) k_fasd_delta_xy<S, ND><<<grid, 256, sm, s>>>(a)
+#define GF_CALL(S, T, ND) k_fasd_delta_xy<S, ND><<<grid, kFasdThreads, sm, s>>>(a)
   GF_FASD_SWITCH(storage, nd, GF_CALL)
 #undef GF_CALL
 }
@@ -57,7 +57,7 @@ void launch_fasd_zt(int storage, int nd, const FasdArgs& a, cudaStream_t s) {
 void launch_fasd_xy_inv_g(int storage, int nd, const FasdArgs& a, cudaStream_t s) {
   const dim3 grid(a.lat.L[2], a.lat.L[3]);
   const size_t sm = plane_smem(storage, a.lat);
-#define GF_CALL(S, T, ND) k_fasd_xy_inv_g<S, ND><<<grid, 256, sm, s>>>(a)
+#define GF_CALL(S, T, ND) k_fasd_xy_inv_g<S, ND><<<grid, kFasdThreads, sm, s>>>(a)
   GF_FASD_SWITCH(storage, nd, GF_CALL)
 #undef GF_CALL
 }
@@ -69,7 +69,6 @@ void launch_fasd_update(int storage, int nd, const FasdArgs& a, cudaStream_t s) 
 #undef GF_CALL
 }
 
-void launch_fasd_bump(const FasdArgs& a, cudaStream_t s) { k_fasd_bump<<<1, 256, 0, s>>>(a); }
 
 size_t fasd_plane_smem(int storage, const LatDev& lat) { return plane_smem(storage, lat); }
 

@@ -288,7 +288,7 @@ struct FasdArgs {
   char* links;            // link storage (FP32-12 or FP64-18) of the lattice
   LatDev lat;
   void* kbuf;             // 4 complex fields, [f][t][z][y][x]
-  char* gbuf;             // g(x): rows 0 and 1, 2 * 3 complex elements, planes [w][idx]
+  char* gbuf;             // g(x): rows 0 and 1, 2 * 3 complex elements, planes [w][lexi]
   float2* plane_F;        // per (z, t) plane, as pairs (hi, lo)
   float2* plane_th;
   const int* unit_planes; // n_units + 1 plane boundaries
