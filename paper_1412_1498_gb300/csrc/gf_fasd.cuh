@@ -88,9 +88,27 @@ __host__ __device__ constexpr int bit_rev(int r, int logL) {
   return o;
 }
 
+// exp(-2 pi i m / L), or its conjugate for sign > 0, for a compile-time power of 2 L <= 64
+// and 0 <= m < L/2, from cos(2 pi k / 64) for k = 0..16 (the values correctly rounded to
+// double, written out below) and the symmetries sin x = cos(pi/2 - x), cos(pi - x) =
+// -cos x.  The register transforms call it with indices fixed at compile time, so every
+// twiddle is a constant in the instruction stream (none loaded, the trivial ones folded).
+template <class T, int L>
+__device__ __forceinline__ cx<T> twiddle(int m, int sign) {
+  constexpr T c[17] = {T(1.0), T(0.9951847266721969), T(0.9807852804032304), T(0.9569403357322088),
+                       T(0.9238795325112867), T(0.881921264348355), T(0.8314696123025452),
+                       T(0.773010453362737), T(0.7071067811865476), T(0.6343932841636455),
+                       T(0.5555702330196022), T(0.47139673682599764), T(0.3826834323650898),
+                       T(0.2902846772544624), T(0.19509032201612828), T(0.0980171403295606), T(0.0)};
+  const int k = m * (64 / L);  // 0 <= k < 32
+  const T co = k <= 16 ? c[k] : -c[32 - k];
+  const T si = k <= 16 ? c[16 - k] : c[k - 16];
+  return {co, sign > 0 ? si : -si};
+}
+
 // decimation in frequency on registers: natural order in, bit-reversed order out
 template <class T, int LOGL>
-__device__ __forceinline__ void dif_reg(cx<T> (&v)[1 << LOGL], const cx<T>* tw, int sign) {
+__device__ __forceinline__ void dif_reg(cx<T> (&v)[1 << LOGL], int sign) {
   constexpr int L = 1 << LOGL;
 #pragma unroll
   for (int span = L / 2; span >= 1; span >>= 1) {
@@ -101,11 +119,7 @@ __device__ __forceinline__ void dif_reg(cx<T> (&v)[1 << LOGL], const cx<T>* tw, 
         const cx<T> a = v[s + j], b = v[s + j + span];
         v[s + j] = cadd(a, b);
         cx<T> e = csub(a, b);
-        if (j != 0) {
-          cx<T> w = tw[j * (L / (2 * span))];  // exp(-2 pi i j / (2 span))
-          if (sign > 0) w.im = -w.im;
-          e = cmul(e, w);
-        }
+        if (j != 0) e = cmul(e, twiddle<T, L>(j * (L / (2 * span)), sign));  // exp(-2 pi i j / (2 span))
         v[s + j + span] = e;
       }
     }
@@ -113,19 +127,19 @@ __device__ __forceinline__ void dif_reg(cx<T> (&v)[1 << LOGL], const cx<T>* tw, 
 }
 
 template <class T, int LOGL>
-__device__ __forceinline__ void fft_line_reg(cx<T>* d, int estride, const cx<T>* tw, int sign) {
+__device__ __forceinline__ void fft_line_reg(cx<T>* d, int estride, int sign) {
   constexpr int L = 1 << LOGL;
   cx<T> v[L];
 #pragma unroll
   for (int k = 0; k < L; ++k) v[k] = d[k * estride];
-  dif_reg<T, LOGL>(v, tw, sign);
+  dif_reg<T, LOGL>(v, sign);
 #pragma unroll
   for (int r = 0; r < L; ++r) d[bit_rev(r, LOGL) * estride] = v[r];
 }
 
 // decimation in time on registers: bit-reversed order in, natural order out
 template <class T, int LOGL>
-__device__ __forceinline__ void dit_reg(cx<T> (&v)[1 << LOGL], const cx<T>* tw, int sign) {
+__device__ __forceinline__ void dit_reg(cx<T> (&v)[1 << LOGL], int sign) {
   constexpr int L = 1 << LOGL;
 #pragma unroll
   for (int span = 1; span < L; span <<= 1) {
@@ -135,11 +149,7 @@ __device__ __forceinline__ void dit_reg(cx<T> (&v)[1 << LOGL], const cx<T>* tw, 
       for (int j = 0; j < span; ++j) {
         const cx<T> a = v[s + j];
         cx<T> b = v[s + j + span];
-        if (j != 0) {
-          cx<T> w = tw[j * (L / (2 * span))];  // exp(-2 pi i j / (2 span))
-          if (sign > 0) w.im = -w.im;
-          b = cmul(b, w);
-        }
+        if (j != 0) b = cmul(b, twiddle<T, L>(j * (L / (2 * span)), sign));  // exp(-2 pi i j / (2 span))
         v[s + j] = cadd(a, b);
         v[s + j + span] = csub(a, b);
       }
@@ -155,19 +165,18 @@ __device__ __forceinline__ double filter_div(double a, double b) { return a / b;
 // mode k scaled in place by coef / (base + s2[k]) (0 where that is not positive: the
 // zero mode), inverse transform by decimation in time (bit-reversed in, natural out).
 template <class T, int LOGL>
-__device__ __forceinline__ void filter_line_reg(cx<T>* d, int estride, const cx<T>* tw, T base,
-                                                const T* s2, T coef) {
+__device__ __forceinline__ void filter_line_reg(cx<T>* d, int estride, T base, const T* s2, T coef) {
   constexpr int L = 1 << LOGL;
   cx<T> v[L];
 #pragma unroll
   for (int k = 0; k < L; ++k) v[k] = d[k * estride];
-  dif_reg<T, LOGL>(v, tw, -1);
+  dif_reg<T, LOGL>(v, -1);
 #pragma unroll
   for (int r = 0; r < L; ++r) {
     const T p2 = base + s2[bit_rev(r, LOGL)];
     v[r] = cscale(v[r], p2 > T(0) ? filter_div(coef, p2) : T(0));
   }
-  dit_reg<T, LOGL>(v, tw, +1);
+  dit_reg<T, LOGL>(v, +1);
 #pragma unroll
   for (int k = 0; k < L; ++k) d[k * estride] = v[k];
 }
@@ -183,11 +192,11 @@ __device__ __forceinline__ void fft_lines_reg(cx<T>* d, const cx<T>* tw, int n_l
   for (int l = threadIdx.x; l < n_lines; l += blockDim.x) {
     cx<T>* p = d + (l & (n_in - 1)) * in_stride + (l >> li) * out_stride;
     switch (logL) {
-      case 1: fft_line_reg<T, 1>(p, estride, tw, sign); break;
-      case 2: fft_line_reg<T, 2>(p, estride, tw, sign); break;
-      case 3: fft_line_reg<T, 3>(p, estride, tw, sign); break;
-      case 4: fft_line_reg<T, 4>(p, estride, tw, sign); break;
-      case 5: fft_line_reg<T, 5>(p, estride, tw, sign); break;
+      case 1: fft_line_reg<T, 1>(p, estride, sign); break;
+      case 2: fft_line_reg<T, 2>(p, estride, sign); break;
+      case 3: fft_line_reg<T, 3>(p, estride, sign); break;
+      case 4: fft_line_reg<T, 4>(p, estride, sign); break;
+      case 5: fft_line_reg<T, 5>(p, estride, sign); break;
       default: break;
     }
   }
@@ -518,11 +527,11 @@ __global__ void __launch_bounds__(256, 2) k_fasd_zt(FasdArgs a) {
       for (int l = threadIdx.x; l < Lz * KX; l += blockDim.x) {     // along t: line (kxl, kz)
         const T base = p2xy[l & mk] + s2z[l >> lk];
         switch (lf) {
-          case 1: filter_line_reg<T, 1>(col + l, pitch, twt, base, s2t, coef); break;
-          case 2: filter_line_reg<T, 2>(col + l, pitch, twt, base, s2t, coef); break;
-          case 3: filter_line_reg<T, 3>(col + l, pitch, twt, base, s2t, coef); break;
-          case 4: filter_line_reg<T, 4>(col + l, pitch, twt, base, s2t, coef); break;
-          default: filter_line_reg<T, 5>(col + l, pitch, twt, base, s2t, coef); break;
+          case 1: filter_line_reg<T, 1>(col + l, pitch, base, s2t, coef); break;
+          case 2: filter_line_reg<T, 2>(col + l, pitch, base, s2t, coef); break;
+          case 3: filter_line_reg<T, 3>(col + l, pitch, base, s2t, coef); break;
+          case 4: filter_line_reg<T, 4>(col + l, pitch, base, s2t, coef); break;
+          default: filter_line_reg<T, 5>(col + l, pitch, base, s2t, coef); break;
         }
       }
       __syncthreads();
@@ -530,11 +539,11 @@ __global__ void __launch_bounds__(256, 2) k_fasd_zt(FasdArgs a) {
     } else {
       for (int l = threadIdx.x; l < KX; l += blockDim.x) {  // along z: line kxl of the slice
         switch (lf) {
-          case 1: filter_line_reg<T, 1>(col + l, KX, twz, p2xy[l], s2z, coef); break;
-          case 2: filter_line_reg<T, 2>(col + l, KX, twz, p2xy[l], s2z, coef); break;
-          case 3: filter_line_reg<T, 3>(col + l, KX, twz, p2xy[l], s2z, coef); break;
-          case 4: filter_line_reg<T, 4>(col + l, KX, twz, p2xy[l], s2z, coef); break;
-          default: filter_line_reg<T, 5>(col + l, KX, twz, p2xy[l], s2z, coef); break;
+          case 1: filter_line_reg<T, 1>(col + l, KX, p2xy[l], s2z, coef); break;
+          case 2: filter_line_reg<T, 2>(col + l, KX, p2xy[l], s2z, coef); break;
+          case 3: filter_line_reg<T, 3>(col + l, KX, p2xy[l], s2z, coef); break;
+          case 4: filter_line_reg<T, 4>(col + l, KX, p2xy[l], s2z, coef); break;
+          default: filter_line_reg<T, 5>(col + l, KX, p2xy[l], s2z, coef); break;
         }
       }
       __syncthreads();
