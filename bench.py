@@ -58,9 +58,9 @@ FLOP_PER_SITE = 2142
 WORKLOAD = "landau-32^4-fp32-12: OR sweep (even+odd, omega 1.7, reunit every 20) + F/theta stop check"
 
 
-def profiled_traffic(profile: str, sources) -> int | None:
-    """DRAM bytes per launch from a committed ncu summary, if the kernel's sources still
-    hash to the value recorded there (otherwise the counters describe another kernel)."""
+def profiled_value(profile: str, sources, key: str) -> int | None:
+    """A counter recorded in a committed ncu summary (`key: value`), if the kernel's sources
+    still hash to the value recorded there (otherwise it describes another kernel)."""
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", profile)
@@ -68,13 +68,21 @@ def profiled_traffic(profile: str, sources) -> int | None:
         return None
     text = open(path).read()
     m_hash = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
-    m_bytes = re.search(r"dram_bytes_per_launch:\s*(\d+)", text)
-    if not m_hash or not m_bytes:
+    m_val = re.search(re.escape(key) + r":\s*(\d+)", text)
+    if not m_hash or not m_val:
         return None
     h = hashlib.sha256()
     for src in sources:
         h.update(open(os.path.join(ROOT, "paper_1412_1498_gb300", "csrc", src), "rb").read())
-    return int(m_bytes.group(1)) if h.hexdigest() == m_hash.group(1) else None
+    return int(m_val.group(1)) if h.hexdigest() == m_hash.group(1) else None
+
+
+def profiled_traffic(profile: str, sources) -> int | None:
+    """DRAM bytes per launch from a committed ncu summary (see profiled_value)."""
+    return profiled_value(profile, sources, "dram_bytes_per_launch")
+
+
+AD_SOURCES = ("gf_device.cuh", "gf_kernels.cuh", "gf_autograd.cuh", "gf_inst_autograd.cu")
 
 
 def reduce_over_ranks(ms_total: float, steps: int, world: int, bytes_per_step: int, dist=None, device=None):
@@ -504,13 +512,16 @@ def run_gpu(args):
         f4.close()
         del f4, U5
 
-    # ---- differentiable F(c), theta(c): forward and backward on the 32^4 FP64 field
+    # ---- differentiable F(c), theta(c): forward and backward on the FP64 field (32^4;
+    # --autograd-lattice L takes L^4, e.g. for a profiler run)
     autograd = None
     if args.autograd:
         from paper_1412_1498_gb300.autograd import functional_theta
-        f5 = gf.GaugeFixer(DIMS, gf.GF_LANDAU, gf.GF_FP64_18, autograd=True, device=dev)
-        f5.upload(make_field(DIMS, EPS_FIELD, 5))
-        c = torch.zeros((V, 8), dtype=torch.float64, device=dev, requires_grad=True)
+        ad_dims = (args.autograd_lattice,) * 4
+        ad_V = args.autograd_lattice ** 4
+        f5 = gf.GaugeFixer(ad_dims, gf.GF_LANDAU, gf.GF_FP64_18, autograd=True, device=dev)
+        f5.upload(make_field(ad_dims, EPS_FIELD, 5))
+        c = torch.zeros((ad_V, 8), dtype=torch.float64, device=dev, requires_grad=True)
         for _ in range(2):
             Fa, _t = functional_theta(c, f5)
             Fa.backward()
@@ -521,7 +532,25 @@ def run_gpu(args):
         Fa.backward()
         r2.record(stream)
         r2.synchronize()
-        autograd = {"lattice": list(DIMS), "forward_ms": r0.elapsed_time(r1), "backward_ms": r1.elapsed_time(r2)}
+        fwd_ms, bwd_ms = r0.elapsed_time(r1), r1.elapsed_time(r2)
+        autograd = {"lattice": list(ad_dims), "forward_ms": fwd_ms, "backward_ms": bwd_ms}
+        # FP64-ALU roofline: FP64 flops per site of each pass (dadd + dmul + 2 dfma thread
+        # instructions, counted by ncu at c = 0 and scaled by the sites) over the event time,
+        # against the FP64 pipe's peak: 2 DFMA per clock per SM (152 SMs at 2070 MHz: 1.26
+        # TFLOP/s, the nominal FP64 rate), at the SM clock sampled during the run
+        fl_f = profiled_value("k_ad_landau_32x4_fp64.md", AD_SOURCES, "fp64_flops_forward_per_site")
+        fl_b = profiled_value("k_ad_landau_32x4_fp64.md", AD_SOURCES, "fp64_flops_backward_per_site")
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks.summary()["sm_mhz"] or 2070.0
+        ad_peak = sms * 4 * mhz * 1e6 / 1e12
+        if fl_f and fl_b:
+            af = fl_f * ad_V / (fwd_ms * 1e-3) / 1e12
+            ab = fl_b * ad_V / (bwd_ms * 1e-3) / 1e12
+            autograd["roofline"] = {
+                "bound": "alu", "unit": "TFLOP/s", "peak": ad_peak,
+                "peak_kind": f"FP64 pipe: 2 DFMA / clock / SM x {sms} SMs at {mhz:.0f} MHz",
+                "forward": {"achieved": af, "frac": af / ad_peak, "fp64_flops_per_site": fl_f},
+                "backward": {"achieved": ab, "frac": ab / ad_peak, "fp64_flops_per_site": fl_b}}
         f5.close()
         del f5
 
@@ -607,6 +636,7 @@ def main():
     # 63 iterations and the final measurement fill four 16-iteration graph replays exactly
     ap.add_argument("--fasd-iters", type=int, default=63)
     ap.add_argument("--autograd", type=int, default=1)
+    ap.add_argument("--autograd-lattice", type=int, default=32, help="L of the L^4 autograd leg")
     ap.add_argument("--skip-units", action="store_true",
                     help="skip the Coulomb 32^3x64 slice and 48-lattice ensemble leg")
     ap.add_argument("--launch", default="", help="fixed launch shape THREADS:register|pipelined "
