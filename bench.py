@@ -420,11 +420,20 @@ def run_gpu(args):
     ms_step = ms_total / args.steps
     # our kernels launched in the timed gf_fix: the opening measurement (two F/theta
     # passes and a finish), three per captured sweep (even and odd half-sweep, the
-    # odd-part finish; replays cover whole 16-sweep graphs) and the even-site pass with
-    # the loop finish, which the graph's conditional node runs on the budget's last
-    # sweep only (every other sweep is decided by its odd part here)
-    graph_sweeps = 16
-    launches = 3 + ((args.steps + graph_sweeps - 1) // graph_sweeps) * graph_sweeps * 3 + 2
+    # odd-part finish) over the replayed graphs, whose lengths (16, 8, 4, 2 or 1 sweeps)
+    # the library picks from the sweeps left as below, and the even-site pass with the
+    # loop finish that the host runs for the budget's last sweep (every other sweep is
+    # decided by its odd part here)
+    captured, left = 0, args.steps
+    while left > 0:
+        k = 0
+        while k < 4 and (16 >> (k + 1)) >= left:
+            k += 1
+        if (16 >> k) - left > 2 and k < 4:
+            k += 1
+        captured += 16 >> k
+        left -= 16 >> k
+    launches = 3 + captured * 3 + 2
 
     # ---- end to end through the C ABI with pinned host buffers: upload, one step, download
     Uh = torch.from_numpy(U).pin_memory()

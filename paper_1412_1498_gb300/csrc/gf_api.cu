@@ -314,9 +314,9 @@ struct gf_handle {
                 // 2: polish buffer in double-float (only inside gf_fix)
   int phase_sweeps[2] = {0, 0};
   int sweeps_done = 0;  // since the last upload: the reunitarisation / check schedule
-  // graphs: one per buffer state (OR), one per set of precision levels of a mixed run,
-  // one for Fourier acceleration
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  // graphs: per buffer state (OR) one of each length 16, 8, 4, 2, 1 sweeps, one per set
+  // of precision levels of a mixed run, one for Fourier acceleration
+  cudaGraphExec_t graph[3][5] = {};
   cudaGraphExec_t graph_mix[8] = {};
   cudaGraphExec_t graph_fasd = nullptr;
   std::string err;
@@ -339,11 +339,12 @@ int fail(gf_handle* h, int code, const std::string& msg) {
 #define GF_CK_LAUNCH(h) GF_CK(h, cudaGetLastError())
 
 void drop_graphs(gf_handle* h) {
-  for (auto& g : h->graph)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (auto& gs : h->graph)
+    for (auto& g : gs)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
   for (auto& g : h->graph_mix)
     if (g) {
       cudaGraphExecDestroy(g);
@@ -536,22 +537,37 @@ int resolve_open_sweep(gf_handle* h) {
   return GF_OK;
 }
 
-int ensure_graph(gf_handle* h) {
-  if (h->graph[h->cur]) return GF_OK;
-  GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = GF_OK, pass = 0;  // kGraphSweeps * 2 half-sweeps: even, so replays keep alternating
-  for (int j = 0; j < kGraphSweeps && rc == GF_OK; ++j) rc = enqueue_loop_sweep(h, h->cap_stream, &pass);
-  cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
-  if (rc != GF_OK) {
-    if (g) cudaGraphDestroy(g);
-    return rc;
+// Capture the loop graphs of the current buffer state, 16 >> k sweeps for k = 0..4 (each
+// an even number of half-sweeps, so replays keep alternating the tile direction), all at
+// once on first use so that no later gf_fix captures inside its run.
+int ensure_graphs(gf_handle* h) {
+  for (int k = 0; k < 5; ++k) {
+    if (h->graph[h->cur][k]) continue;
+    GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+    int rc = GF_OK, pass = 0;
+    for (int j = 0; j < (kGraphSweeps >> k) && rc == GF_OK; ++j) rc = enqueue_loop_sweep(h, h->cap_stream, &pass);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (rc != GF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    e = cudaGraphInstantiate(&h->graph[h->cur][k], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   }
-  if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
-  e = cudaGraphInstantiate(&h->graph[h->cur], g, 0);
-  cudaGraphDestroy(g);
-  if (e != cudaSuccess) return fail(h, GF_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   return GF_OK;
+}
+
+// The graph for the next replay when `left` sweeps of the budget remain: the shortest
+// length >= left, halved when that would run more than two gated sweeps past the budget
+// (a gated sweep costs about three idle launches, a further replay one host round trip).
+int graph_index(int left) {
+  int k = 0;  // 16 >> k sweeps
+  while (k < 4 && (kGraphSweeps >> (k + 1)) >= left) ++k;
+  if ((kGraphSweeps >> k) - left > 2 && k < 4) ++k;
+  return k;
 }
 
 int read_state(gf_handle* h, DevState* out) {
@@ -580,9 +596,9 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   int rc = enqueue_measure_all(h, FINISH_RESET);
   if (rc != GF_OK) return rc;
   if ((rc = read_state(h, &s)) != GF_OK) return rc;
-  if ((rc = ensure_graph(h)) != GF_OK) return rc;
+  if ((rc = ensure_graphs(h)) != GF_OK) return rc;
   while (s.n_active > 0 && s.sweep < s.limit) {
-    GF_CK(h, cudaGraphLaunch(h->graph[h->cur], h->stream));
+    GF_CK(h, cudaGraphLaunch(h->graph[h->cur][graph_index(s.limit - s.sweep)], h->stream));
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
     if (s.hold) {
       if ((rc = resolve_open_sweep(h)) != GF_OK) return rc;
