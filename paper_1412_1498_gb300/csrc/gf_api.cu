@@ -37,6 +37,8 @@ void launch_split_to_fp64(char* links, const LatDev& lat, cudaStream_t s);
 constexpr int kSplit18 = 100;
 
 cudaError_t prepare_fasd(int storage, int nd, const LatDev& lat);
+int fasd_xy_prefetch(int storage, int nd);
+int fasd_zt_prefetch(int storage, int nd);
 void launch_fasd_delta_xy(int storage, int nd, const FasdArgs& a, cudaStream_t s);
 void launch_fasd_finish(const FasdArgs& a, cudaStream_t s);
 void launch_fasd_zt(int storage, int nd, const FasdArgs& a, cudaStream_t s);
@@ -886,6 +888,8 @@ FasdArgs fasd_args(gf_handle* h, bool loop, int mode) {
   const double nfft = h->nd == 4 ? (double)a.lat.V : 2.0 * a.lat.V3h;
   a.coef = 0.5 * h->alpha * (4.0 * h->nd) / nfft;
   a.kx = fasd_kx(a.lat, h->nd, h->storage == GF_FP64_18 ? 16 : 8);
+  a.xy_prefetch = fasd_xy_prefetch(h->storage, h->nd);
+  a.zt_prefetch = fasd_zt_prefetch(h->storage, h->nd);
   return a;
 }
 

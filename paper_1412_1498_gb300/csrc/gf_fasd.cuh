@@ -469,140 +469,232 @@ __global__ void __launch_bounds__(256) k_fasd_finish(FasdArgs a) {
   }
 }
 
+// Asynchronous copies of k-space elements into shared memory (8-byte complex floats,
+// 16-byte complex doubles; both addresses aligned to the element).
+template <class T>
+__device__ __forceinline__ void cp_async_cx(cx<T>* s, const cx<T>* g) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(s);
+  if constexpr (sizeof(cx<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all_groups() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ------------------------------------------------------------------------- C: FFT z(t), filter
-// Block: one field, one ky, KX consecutive kx (KX = a.kx <= 8, chosen on the host so the
-// block fits in shared memory) and (Coulomb) one t.  Shared layout
+// Item: one field, one ky, KX consecutive kx (a.kx, chosen on the host so that two items'
+// columns fit in shared memory) and (Coulomb) one t.  Shared layout
 // col[kxl + KX z + (KX Lz + KX) tl]: the pad keeps both transform directions free of bank
-// conflicts.
+// conflicts.  Persistent blocks walk the items; with a.zt_prefetch the next item's
+// columns arrive by cp.async in a second buffer while the current one is transformed.
+template <class T>
+__device__ __forceinline__ void column_issue(const FasdArgs& a, int nd, int kx0, int ky, int f, int t0,
+                                             cx<T>* col) {
+  const LatDev& lat = a.lat;
+  const int Lx = lat.L[0], Lz = lat.L[2], lz = a.logL[2];
+  const int KX = a.kx, lk = __ffs(KX) - 1, pitch = KX * Lz + KX;
+  const int n = (nd == 4 ? lat.L[3] : 1) << (lz + lk);
+  const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf) + f * lat.V;
+  const long long P = (long long)Lx * lat.L[1];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int kxl = i & (KX - 1), z = (i >> lk) & (Lz - 1), tl = i >> (lk + lz);
+    cp_async_cx(col + kxl + KX * z + pitch * tl,
+                kb + P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl);
+  }
+}
+
 template <class T, int ND>
-__global__ void __launch_bounds__(256, 2) k_fasd_zt(FasdArgs a) {
+__global__ void __launch_bounds__(kFasdThreads, 2) k_fasd_zt(FasdArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ cx<T> twz[32], twt[32];
-  __shared__ T s2z[64], s2t[64];   // 4 sin^2(pi k / L) along z and t
+  __shared__ T s2x[64], s2y[64], s2z[64], s2t[64];   // 4 sin^2(pi k / L) along x, y, z, t
   if (!fasd_running(a.st)) return;
   const LatDev& lat = a.lat;
   const int Lx = lat.L[0], Ly = lat.L[1], Lz = lat.L[2], Lt = lat.L[3];
   const int lz = a.logL[2];
-  const int KX = a.kx, lk = __ffs(KX) - 1;
-  const int kx0 = blockIdx.x * KX, ky = blockIdx.y;
-  const int f = ND == 4 ? (int)blockIdx.z : (int)blockIdx.z & 3;
-  const int t0 = ND == 4 ? 0 : (int)blockIdx.z >> 2, nt = ND == 4 ? Lt : 1;
-  if (ND == 3 && a.active && !a.active[t0]) return;
-  cx<T>* col = reinterpret_cast<cx<T>*>(smraw);
+  const int KX = a.kx, lk = __ffs(KX) - 1, nxg = Lx / KX;
+  const int nt = ND == 4 ? Lt : 1;
+  const int n_items = nxg * Ly * (ND == 4 ? 4 : 4 * Lt);
   const int pitch = KX * Lz + KX;  // 2 pitch = 2 KX (Lz + 1): z-line groups split the banks evenly
+  const int n = nt << (lz + lk);   // elements of an item
+  cx<T>* buf[2] = {reinterpret_cast<cx<T>*>(smraw), reinterpret_cast<cx<T>*>(smraw) + pitch * nt};
   twiddles(twz, lz);
   if (ND == 4) twiddles(twt, a.logL[3]);
-  for (int k = threadIdx.x; k < Lz; k += blockDim.x) {
-    const T sn = sinpi((T)k / (T)Lz);
-    s2z[k] = T(4) * sn * sn;
+  for (int k = threadIdx.x; k < 64; k += blockDim.x) {
+    T sn;
+    if (k < Lx) { sn = sinpi((T)k / (T)Lx); s2x[k] = T(4) * sn * sn; }
+    if (k < Ly) { sn = sinpi((T)k / (T)Ly); s2y[k] = T(4) * sn * sn; }
+    if (k < Lz) { sn = sinpi((T)k / (T)Lz); s2z[k] = T(4) * sn * sn; }
+    if (ND == 4 && k < Lt) { sn = sinpi((T)k / (T)Lt); s2t[k] = T(4) * sn * sn; }
   }
-  if (ND == 4)
-    for (int k = threadIdx.x; k < Lt; k += blockDim.x) {
-      const T sn = sinpi((T)k / (T)Lt);
-      s2t[k] = T(4) * sn * sn;
-    }
-  __shared__ T p2xy[8];  // 4 sin^2 along x + along y for the block's kx columns
-  if ((int)threadIdx.x < KX) {
-    const T sx = sinpi((T)(kx0 + (int)threadIdx.x) / (T)Lx), sy = sinpi((T)ky / (T)Ly);
-    p2xy[threadIdx.x] = T(4) * sx * sx + T(4) * sy * sy;
-  }
+  // item -> (kx0, ky, f, t0); Coulomb items of converged slices are skipped
+  auto decode = [&](int it, int& kx0, int& ky, int& f, int& t0) {
+    kx0 = (it % nxg) * KX;
+    const int r = it / nxg;
+    ky = r % Ly;
+    const int fz = r / Ly;
+    f = ND == 4 ? fz : (fz & 3);
+    t0 = ND == 4 ? 0 : (fz >> 2);
+  };
+  auto skip = [&](int it) {
+    if (ND == 3 && a.active)
+      while (it < n_items && !a.active[(it / (nxg * Ly)) >> 2]) it += gridDim.x;
+    return it;
+  };
+  int it = skip((int)blockIdx.x);
+  if (it >= n_items) return;
+  int kx0, ky, f, t0;
+  decode(it, kx0, ky, f, t0);
+  int cur = 0;
+  column_issue<T>(a, ND, kx0, ky, f, t0, buf[0]);
+  cp_async_commit_group();
+  cp_async_wait_all_groups();
   __syncthreads();
-  cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf) + f * lat.V;
-  const long long P = (long long)Lx * Ly;
-  const int n = nt << (lz + lk);
-  const int mz = Lz - 1, mk = KX - 1;
-#pragma unroll 16
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {  // 16 loads in flight per thread
-    const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);
-    col[kxl + KX * z + pitch * tl] = kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl];
-  }
-  __syncthreads();
+  const T coef = (T)a.coef;
   const int lf = ND == 4 ? a.logL[3] : lz;  // the direction transformed last
-  if (lf <= 5 && lz <= 5) {
-    // lines through registers; the last direction is transformed, filtered and
-    // transformed back in one pass (filter_line_reg)
-    const T coef = (T)a.coef;
-    if (ND == 4) {
-      fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);  // along z
-      for (int l = threadIdx.x; l < Lz * KX; l += blockDim.x) {     // along t: line (kxl, kz)
-        const T base = p2xy[l & mk] + s2z[l >> lk];
-        switch (lf) {
-          case 1: filter_line_reg<T, 1>(col + l, pitch, base, s2t, coef); break;
-          case 2: filter_line_reg<T, 2>(col + l, pitch, base, s2t, coef); break;
-          case 3: filter_line_reg<T, 3>(col + l, pitch, base, s2t, coef); break;
-          case 4: filter_line_reg<T, 4>(col + l, pitch, base, s2t, coef); break;
-          default: filter_line_reg<T, 5>(col + l, pitch, base, s2t, coef); break;
+  const int mz = Lz - 1, mk = KX - 1;
+  const long long P = (long long)Lx * Ly;
+  while (it < n_items) {
+    const int itn = skip(it + (int)gridDim.x);
+    int kx0n = 0, kyn = 0, fn = 0, t0n = 0;
+    if (itn < n_items) decode(itn, kx0n, kyn, fn, t0n);
+    if (a.zt_prefetch && itn < n_items) column_issue<T>(a, ND, kx0n, kyn, fn, t0n, buf[cur ^ 1]);
+    cp_async_commit_group();
+    cx<T>* col = buf[cur];
+    const T pxy = s2y[ky];
+    if (lf <= 5 && lz <= 5) {
+      // lines through registers; the last direction is transformed, filtered and
+      // transformed back in one pass (filter_line_reg)
+      if (ND == 4) {
+        fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);  // along z
+        for (int l = threadIdx.x; l < Lz * KX; l += blockDim.x) {     // along t: line (kxl, kz)
+          const T base = s2x[kx0 + (l & mk)] + pxy + s2z[l >> lk];
+          switch (lf) {
+            case 1: filter_line_reg<T, 1>(col + l, pitch, base, s2t, coef); break;
+            case 2: filter_line_reg<T, 2>(col + l, pitch, base, s2t, coef); break;
+            case 3: filter_line_reg<T, 3>(col + l, pitch, base, s2t, coef); break;
+            case 4: filter_line_reg<T, 4>(col + l, pitch, base, s2t, coef); break;
+            default: filter_line_reg<T, 5>(col + l, pitch, base, s2t, coef); break;
+          }
         }
+        __syncthreads();
+        fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
+      } else {
+        for (int l = threadIdx.x; l < KX; l += blockDim.x) {  // along z: line kxl of the slice
+          const T base = s2x[kx0 + l] + pxy;
+          switch (lf) {
+            case 1: filter_line_reg<T, 1>(col + l, KX, base, s2z, coef); break;
+            case 2: filter_line_reg<T, 2>(col + l, KX, base, s2z, coef); break;
+            case 3: filter_line_reg<T, 3>(col + l, KX, base, s2z, coef); break;
+            case 4: filter_line_reg<T, 4>(col + l, KX, base, s2z, coef); break;
+            default: filter_line_reg<T, 5>(col + l, KX, base, s2z, coef); break;
+          }
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
     } else {
-      for (int l = threadIdx.x; l < KX; l += blockDim.x) {  // along z: line kxl of the slice
-        switch (lf) {
-          case 1: filter_line_reg<T, 1>(col + l, KX, p2xy[l], s2z, coef); break;
-          case 2: filter_line_reg<T, 2>(col + l, KX, p2xy[l], s2z, coef); break;
-          case 3: filter_line_reg<T, 3>(col + l, KX, p2xy[l], s2z, coef); break;
-          case 4: filter_line_reg<T, 4>(col + l, KX, p2xy[l], s2z, coef); break;
-          default: filter_line_reg<T, 5>(col + l, KX, p2xy[l], s2z, coef); break;
-        }
+      fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);          // along z
+      if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, -1);  // along t
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int kxl = i & mk, kz = (i >> lk) & mz, kt = i >> (lk + lz);
+        T p2 = s2x[kx0 + kxl] + pxy + s2z[kz];
+        if (ND == 4) p2 += s2t[kt];
+        const T fac = p2 > T(0) ? coef / p2 : T(0);
+        const int c = kxl + KX * kz + pitch * kt;
+        col[c] = cscale(col[c], fac);
       }
       __syncthreads();
+      if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, +1);
+      fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
     }
-  } else {
-    fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);          // along z
-    if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, -1);  // along t
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      const int kxl = i & mk, kz = (i >> lk) & mz, kt = i >> (lk + lz);
-      T p2 = p2xy[kxl] + s2z[kz];
-      if (ND == 4) p2 += s2t[kt];
-      const T fac = p2 > T(0) ? (T)a.coef / p2 : T(0);
-      const int c = kxl + KX * kz + pitch * kt;
-      col[c] = cscale(col[c], fac);
-    }
-    __syncthreads();
-    if (ND == 4) fft_lines_reg(col, twt, Lz * KX, a.logL[3], Lz * KX, 1, 0, pitch, +1);
-    fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
-  }
+    cx<T>* kb = reinterpret_cast<cx<T>*>(a.kbuf) + f * lat.V;
 #pragma unroll 8
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);
-    kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl] = col[kxl + KX * z + pitch * tl];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int kxl = i & mk, z = (i >> lk) & mz, tl = i >> (lk + lz);
+      kb[P * (z + (long long)Lz * (t0 + tl)) + (long long)Lx * ky + kx0 + kxl] = col[kxl + KX * z + pitch * tl];
+    }
+    if (!a.zt_prefetch && itn < n_items) {
+      __syncthreads();  // every thread is done with the single buffer
+      column_issue<T>(a, ND, kx0n, kyn, fn, t0n, buf[cur]);
+      cp_async_commit_group();
+    }
+    cp_async_wait_all_groups();
+    __syncthreads();
+    if (a.zt_prefetch) cur ^= 1;
+    it = itn;
+    kx0 = kx0n; ky = kyn; f = fn; t0 = t0n;
   }
 }
 
 // ------------------------------------------------------------------------- D: inverse xy, g
+// Start the copies of one (z, t) plane of the four k-space fields into pl[4][Ly][pitch].
+template <class T>
+__device__ __forceinline__ void plane_issue(const FasdArgs& a, int plane, cx<T>* pl) {
+  const LatDev& lat = a.lat;
+  const int Lx = lat.L[0], Ly = lat.L[1], P = Lx * Ly, pitch = Lx + 1;
+  const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf) + (long long)P * plane;
+  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {
+    const int f = i >> (a.logL[0] + a.logL[1]), j = i & (P - 1);
+    cp_async_cx(pl + (f * Ly + (j >> a.logL[0])) * pitch + (j & (Lx - 1)), kb + f * lat.V + j);
+  }
+}
+
+// Persistent blocks walk the (z, t) planes (plane = z + Lz t; Coulomb: the active slices'
+// only); with a.xy_prefetch the next plane's k-space arrives by cp.async in a second
+// buffer while the current one is transformed, so the copies' latency hides behind the
+// transforms.
 template <int S, int ND>
-__global__ void __launch_bounds__(kFasdThreads, S == GF_FP64_18 ? 2 : 4) k_fasd_xy_inv_g(FasdArgs a) {
+__global__ void __launch_bounds__(kFasdThreads, S == GF_FP64_18 ? 2 : 3) k_fasd_xy_inv_g(FasdArgs a) {
   using St = Store<S>;
   using T = typename St::T;
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ cx<T> twx[32], twy[32];
   if (!fasd_running(a.st)) return;
   const LatDev& lat = a.lat;
-  const int z = blockIdx.x, t = blockIdx.y;
-  if (ND == 3 && a.active && !a.active[t]) return;
   const int Lx = lat.L[0], Ly = lat.L[1], P = Lx * Ly;
   const int pitch = Lx + 1;
-  cx<T>* pl = reinterpret_cast<cx<T>*>(smraw);  // [4][Ly][pitch]
+  const int n_planes = lat.L[2] * lat.L[3];
+  cx<T>* buf[2] = {reinterpret_cast<cx<T>*>(smraw), reinterpret_cast<cx<T>*>(smraw) + 4 * Ly * pitch};
   twiddles(twx, a.logL[0]);
   twiddles(twy, a.logL[1]);
-  const cx<T>* kb = reinterpret_cast<const cx<T>*>(a.kbuf);
-  const long long plane0 = (long long)P * (z + lat.L[2] * (long long)t);
-#pragma unroll 16
-  for (int i = threadIdx.x; i < 4 * P; i += blockDim.x) {  // 16 loads in flight per thread
-    const int f = i >> (a.logL[0] + a.logL[1]), j = i & (P - 1);
-    pl[(f * Ly + (j >> a.logL[0])) * pitch + (j & (Lx - 1))] = kb[f * lat.V + plane0 + j];
-  }
+  auto skip = [&](int p) {  // first plane >= p of this block's stride that needs work
+    if (ND == 3 && a.active)
+      while (p < n_planes && !a.active[p >> a.logL[2]]) p += gridDim.x;
+    return p;
+  };
+  int p = skip((int)blockIdx.x);
+  if (p >= n_planes) return;
+  int cur = 0;
+  plane_issue<T>(a, p, buf[0]);
+  cp_async_commit_group();
+  cp_async_wait_all_groups();
   __syncthreads();
-  fft_lines_reg(pl, twy, 4 * Lx, a.logL[1], Lx, 1, Ly * pitch, pitch, +1);
-  fft_lines_reg(pl, twx, 4 * Ly, a.logL[0], 1, 0, pitch, 1, +1);
-  for (int i = threadIdx.x; i < P; i += blockDim.x) {
-    const int x = i & (Lx - 1), y = i >> a.logL[0];
-    // Delta~ (already scaled by alpha/2 p^2_max/p^2/N): anti-Hermitian, traceless
-    const int r = y * pitch + x, fs = Ly * pitch;
-    cx<T> g[9];
-    g_from_delta<T>(pl[r], pl[fs + r], pl[2 * fs + r], pl[3 * fs + r], g);
-    g_store<T>(a.gbuf, lat.V, plane0 + i, g);
+  while (p < n_planes) {
+    const int pn = skip(p + (int)gridDim.x);
+    if (a.xy_prefetch && pn < n_planes) plane_issue<T>(a, pn, buf[cur ^ 1]);
+    cp_async_commit_group();
+    cx<T>* pl = buf[cur];
+    fft_lines_reg(pl, twy, 4 * Lx, a.logL[1], Lx, 1, Ly * pitch, pitch, +1);
+    fft_lines_reg(pl, twx, 4 * Ly, a.logL[0], 1, 0, pitch, 1, +1);
+    const long long plane0 = (long long)P * p;
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+      const int x = i & (Lx - 1), y = i >> a.logL[0];
+      // Delta~ (already scaled by alpha/2 p^2_max/p^2/N): anti-Hermitian, traceless
+      const int r = y * pitch + x, fs = Ly * pitch;
+      cx<T> g[9];
+      g_from_delta<T>(pl[r], pl[fs + r], pl[2 * fs + r], pl[3 * fs + r], g);
+      g_store<T>(a.gbuf, lat.V, plane0 + i, g);
+    }
+    if (!a.xy_prefetch && pn < n_planes) {
+      __syncthreads();  // every thread is done with the single buffer
+      plane_issue<T>(a, pn, buf[cur]);
+      cp_async_commit_group();
+    }
+    cp_async_wait_all_groups();
+    __syncthreads();
+    if (a.xy_prefetch) cur ^= 1;
+    p = pn;
   }
 }
 

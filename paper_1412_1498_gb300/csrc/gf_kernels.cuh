@@ -307,15 +307,20 @@ struct FasdArgs {
   int mode;               // finish: FINISH_LOOP or FINISH_MEASURE
   int logL[4];
   int kx;                 // kx columns per block of the z/t transform (power of 2, <= 8)
+  int xy_prefetch;        // inverse x/y transform: two plane buffers (next plane prefetched)
+  int zt_prefetch;        // z/t transform: two column buffers (next item prefetched)
   double coef;            // alpha / 2 * p^2_max / N_fft
 };
 
-// kx columns per z/t-transform block: up to 8, halved until the block's columns
-// (nt x (KX Lz + KX) elements of c bytes) fit in 200 KB of shared memory
+// kx columns per z/t-transform item: up to 4 (Landau: 4 x Lz lines per direction, one
+// per thread of a 128-thread block at 32^4) or 32 (Coulomb: one z-line per column),
+// halved until two items' columns (nt x (KX Lz + KX) elements of c bytes each) fit in
+// 110 KB of shared memory, so that two double-buffered blocks share an SM
 inline int fasd_kx(const LatDev& lat, int nd, size_t c) {
-  int kx = lat.L[0] < 8 ? lat.L[0] : 8;
+  const int cap = nd == 4 ? 4 : 32;
+  int kx = lat.L[0] < cap ? lat.L[0] : cap;
   const size_t nt = nd == 4 ? lat.L[3] : 1;
-  while (kx > 1 && nt * ((size_t)kx * lat.L[2] + kx) * c > 200 * 1024) kx /= 2;
+  while (kx > 1 && 2 * nt * ((size_t)kx * lat.L[2] + kx) * c > 110 * 1024) kx /= 2;
   return kx;
 }
 
