@@ -419,12 +419,12 @@ def run_gpu(args):
     ms_total, value = reduce_over_ranks(ms_total, args.steps, world, bytes_per_step, dist, dev)
     ms_step = ms_total / args.steps
     # our kernels launched in the timed gf_fix: the opening measurement (two F/theta
-    # passes and a finish), three per captured sweep (even and odd half-sweep, the
-    # odd-part finish) over the replayed graphs, whose lengths (16, 8, 4, 2 or 1 sweeps)
-    # the library picks from the sweeps left as below, and the even-site pass with the
-    # loop finish that the host runs for the budget's last sweep (every other sweep is
-    # decided by its odd part here)
-    captured, left = 0, args.steps
+    # passes and a finish), then per replayed graph three per captured sweep (even and
+    # odd half-sweep, the odd-part finish) and the even-site pass with the loop finish
+    # that close the graph (they work on the budget's last sweep only: every other sweep
+    # is decided by its odd part here); the library picks the graph lengths (16, 8, 4,
+    # 2 or 1 sweeps) from the sweeps left as below
+    captured, replays, left = 0, 0, args.steps
     while left > 0:
         k = 0
         while k < 4 and (16 >> (k + 1)) >= left:
@@ -432,8 +432,9 @@ def run_gpu(args):
         if (16 >> k) - left > 2 and k < 4:
             k += 1
         captured += 16 >> k
+        replays += 1
         left -= 16 >> k
-    launches = 3 + captured * 3 + 2
+    launches = 3 + captured * 3 + 2 * replays
 
     # ---- end to end through the C ABI with pinned host buffers: upload, one step, download
     Uh = torch.from_numpy(U).pin_memory()

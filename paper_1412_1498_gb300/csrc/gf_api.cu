@@ -321,6 +321,10 @@ struct gf_handle {
   cudaGraphExec_t graph[3][5] = {};
   cudaGraphExec_t graph_mix[8] = {};
   cudaGraphExec_t graph_fasd = nullptr;
+  // loop-state snapshots of the replays in flight (pinned host ring) and their events
+  DevState* st_host = nullptr;
+  cudaEvent_t st_ev[2] = {nullptr, nullptr};
+  int last_active = 0;  // active units when the last OR loop (run_phase / run_mixed) ended
   std::string err;
 };
 
@@ -541,13 +545,22 @@ int resolve_open_sweep(gf_handle* h) {
 
 // Capture the loop graphs of the current buffer state, 16 >> k sweeps for k = 0..4 (each
 // an even number of half-sweeps, so replays keep alternating the tile direction), all at
-// once on first use so that no later gf_fix captures inside its run.
+// once on first use so that no later gf_fix captures inside its run.  Each graph ends
+// with the even-site pass and the loop finish, which act only on a sweep left open: a
+// replay ends with every sweep resolved (the rest of a replay after an open sweep does
+// nothing), so the host reads the state without resolving anything.
 int ensure_graphs(gf_handle* h) {
   for (int k = 0; k < 5; ++k) {
     if (h->graph[h->cur][k]) continue;
     GF_CK(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
     int rc = GF_OK, pass = 0;
     for (int j = 0; j < (kGraphSweeps >> k) && rc == GF_OK; ++j) rc = enqueue_loop_sweep(h, h->cap_stream, &pass);
+    if (rc == GF_OK) {
+      launch_measure(cur_storage(h), h->nd, h->variant, measure_args(h, 0, true, 0), h->n_tiles, h->threads,
+                     h->cap_stream);
+      launch_finish(finish_args(h, FINISH_LOOP), h->cap_stream);
+      if (cudaGetLastError() != cudaSuccess) rc = fail(h, GF_ECUDA, "launch in the loop capture failed");
+    }
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
     if (rc != GF_OK) {
@@ -580,6 +593,11 @@ int read_state(gf_handle* h, DevState* out) {
 
 // One phase of Algorithm 1 on the current buffer: measure, then sweeps until every
 // unit is below eps or `budget` sweeps were done.  *done receives the sweeps done.
+// Two graph replays are kept in flight: each one's loop state is copied to a pinned
+// host slot behind it, and the host reads a replay's state while the next one runs; the
+// replay after the one that ends the run (every unit below eps) finds nothing to do.
+// Replays are planned as if all their sweeps ran; a sweep left open idles the rest of
+// its replay, so whenever nothing is in flight the plan restarts from the sweeps done.
 int run_phase(gf_handle* h, double eps, int budget, int* done) {
   DevState s{};
   const int offset = h->sweeps_done;
@@ -597,18 +615,37 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   GF_CK(h, cudaMemcpyAsync(h->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream));
   int rc = enqueue_measure_all(h, FINISH_RESET);
   if (rc != GF_OK) return rc;
-  if ((rc = read_state(h, &s)) != GF_OK) return rc;
   if ((rc = ensure_graphs(h)) != GF_OK) return rc;
-  while (s.n_active > 0 && s.sweep < s.limit) {
-    GF_CK(h, cudaGraphLaunch(h->graph[h->cur][graph_index(s.limit - s.sweep)], h->stream));
-    if ((rc = read_state(h, &s)) != GF_OK) return rc;
-    if (s.hold) {
-      if ((rc = resolve_open_sweep(h)) != GF_OK) return rc;
-      if ((rc = read_state(h, &s)) != GF_OK) return rc;
+  int planned = 0, inflight = 0, w = 0, r = 0;
+  bool stop = budget == 0;
+  for (;;) {
+    while (!stop && inflight < 2 && planned < budget) {
+      const int k = graph_index(budget - planned);
+      GF_CK(h, cudaGraphLaunch(h->graph[h->cur][k], h->stream));
+      GF_CK(h, cudaMemcpyAsync(h->st_host + w, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+      GF_CK(h, cudaEventRecord(h->st_ev[w], h->stream));
+      planned += kGraphSweeps >> k;
+      w ^= 1;
+      ++inflight;
     }
+    if (inflight == 0) break;
+    GF_CK(h, cudaEventSynchronize(h->st_ev[r]));
+    s = h->st_host[r];
+    r ^= 1;
+    --inflight;
+    if (s.n_active == 0 || s.sweep >= s.limit) stop = true;
+    if (inflight == 0) planned = s.sweep - offset;
+  }
+  if (budget == 0 || planned == 0) {
+    if ((rc = read_state(h, &s)) != GF_OK) return rc;
+  }
+  if (s.hold) {  // not expected: every replay ends with its open sweep resolved
+    if ((rc = resolve_open_sweep(h)) != GF_OK) return rc;
+    if ((rc = read_state(h, &s)) != GF_OK) return rc;
   }
   *done = s.sweep - offset;
   h->hist_n = s.hist_n;
+  h->last_active = s.n_active;
   return GF_OK;
 }
 
@@ -841,6 +878,7 @@ int run_mixed(gf_handle* h, double eps, int budget, int* sweeps_fp32, int* sweep
   if ((rc = read_state(h, &s)) != GF_OK) return rc;
   h->cur = 1;
   h->hist_n = s.hist_n;
+  h->last_active = s.n_active;
   *sweeps = s.sweep;
   return GF_OK;
 }
@@ -1017,6 +1055,15 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(GF_ECUDA, "cudaStreamCreate failed");
+  if (cudaHostAlloc((void**)&h->st_host, 2 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) {
+    h->st_host = nullptr;
+    return bail(GF_ENOMEM, "pinned host memory for the loop state");
+  }
+  for (auto& ev : h->st_ev)
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+      ev = nullptr;
+      return bail(GF_ECUDA, "event creation failed");
+    }
   {
     cudaError_t e = prepare_sweep_pipe();
     if (e != cudaSuccess) return bail(GF_ECUDA, std::string("sweep kernel set-up: ") + cudaGetErrorString(e));
@@ -1126,6 +1173,9 @@ void gf_destroy(gf_handle* h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  for (auto& ev : h->st_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (h->st_host) cudaFreeHost(h->st_host);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;
 }
@@ -1265,9 +1315,7 @@ int gf_fix(gf_handle* h, double eps, int maxiter, int* iters, double* F, double*
     h->phase_sweeps[h->cur == 1 || is_fp64_storage(h->storage) ? 1 : 0] = done;
   }
   if ((rc = copy_out(h, F, theta, nullptr, nullptr, iters)) != GF_OK) return rc;
-  DevState s{};
-  if ((rc = read_state(h, &s)) != GF_OK) return rc;
-  return s.n_active > 0 ? GF_ENOTCONVERGED : GF_OK;
+  return h->last_active > 0 ? GF_ENOTCONVERGED : GF_OK;
 }
 
 int gf_set_omega(gf_handle* h, double omega) {

@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
     if (!(n_active > 0 && sweep < limit)) return;  // uniform over the grid: no ticket taken
     if (a.mode == FINISH_ODD && hold) return;        // the previous sweep is still open
     check = ((sweep + 1) % ci) == 0 || sweep + 1 == limit;  // state_check_sweep
-    if (a.mode == FINISH_LOOP && closed) return;  // written by the previous launch
+    // the loop finish serves an open sweep only (written by the odd-part finish), so a
+    // second one after the sweep was resolved does nothing
+    if (a.mode == FINISH_LOOP && (closed || !hold)) return;
   }
   bool reduce;
   // a sweep without a check is closed by the odd-part finish (counts, no sums)

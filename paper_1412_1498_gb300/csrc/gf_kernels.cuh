@@ -463,7 +463,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   using T = typename St::T;
   constexpr int NE = St::NE;
   __shared__ double red[64];
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
+  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact || !a.st->hold)) return;
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
   if (a.active && a.active[tile.w] != a.level) return;

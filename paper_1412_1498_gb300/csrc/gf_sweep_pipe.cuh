@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
   extern __shared__ float4 sm[];
   __shared__ double red[2][64];  // alternate per tile sum, as in k_or_sweep_pipe
   int rb = 0;
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact)) return;
+  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact || !a.st->hold)) return;
   int k = blockIdx.x;
   if (k >= a.n_tiles) return;
   const int B = blockDim.x;
