@@ -616,7 +616,7 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   int rc = enqueue_measure_all(h, FINISH_RESET);
   if (rc != GF_OK) return rc;
   if ((rc = ensure_graphs(h)) != GF_OK) return rc;
-  int planned = 0, inflight = 0, w = 0, r = 0;
+  int planned = 0, inflight = 0, w = 0, r = 0, drained_at = -1;
   bool stop = budget == 0;
   for (;;) {
     while (!stop && inflight < 2 && planned < budget) {
@@ -634,7 +634,13 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
     r ^= 1;
     --inflight;
     if (s.n_active == 0 || s.sweep >= s.limit) stop = true;
-    if (inflight == 0) planned = s.sweep - offset;
+    if (inflight == 0) {
+      // every replay sweeps at least once while units are active: no progress since the
+      // previous drain means a broken loop state, not a slow unit
+      if (!stop && s.sweep == drained_at) return fail(h, GF_ECUDA, "sweep loop made no progress");
+      drained_at = s.sweep;
+      planned = s.sweep - offset;
+    }
   }
   if (budget == 0 || planned == 0) {
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
