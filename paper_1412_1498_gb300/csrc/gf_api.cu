@@ -324,6 +324,7 @@ struct gf_handle {
   // loop-state snapshots of the replays in flight (pinned host ring) and their events
   DevState* st_host = nullptr;
   cudaEvent_t st_ev[2] = {nullptr, nullptr};
+  char* out_host = nullptr;  // pinned staging of the values gf_fix / gf_functional_theta return
   int last_active = 0;  // active units when the last OR loop (run_phase / run_mixed) ended
   std::string err;
 };
@@ -889,13 +890,26 @@ int run_mixed(gf_handle* h, double eps, int budget, int* sweeps_fp32, int* sweep
   return GF_OK;
 }
 
+// The requested results through the handle's pinned staging: asynchronous copies and one
+// synchronisation (a copy into pageable memory would block on each call).
 int copy_out(gf_handle* h, double* F, double* theta, double* uF, double* uT, int* iters) {
-  if (F) GF_CK(h, cudaMemcpyAsync(F, h->d_lF, sizeof(double) * h->n_lat, cudaMemcpyDeviceToHost, h->stream));
-  if (theta) GF_CK(h, cudaMemcpyAsync(theta, h->d_lT, sizeof(double) * h->n_lat, cudaMemcpyDeviceToHost, h->stream));
-  if (uF) GF_CK(h, cudaMemcpyAsync(uF, h->d_uF, sizeof(double) * h->n_units, cudaMemcpyDeviceToHost, h->stream));
-  if (uT) GF_CK(h, cudaMemcpyAsync(uT, h->d_uT, sizeof(double) * h->n_units, cudaMemcpyDeviceToHost, h->stream));
-  if (iters) GF_CK(h, cudaMemcpyAsync(iters, h->d_iters, sizeof(int) * h->n_units, cudaMemcpyDeviceToHost, h->stream));
+  double* sF = reinterpret_cast<double*>(h->out_host);
+  double* sT = sF + h->n_lat;
+  double* suF = sT + h->n_lat;
+  double* suT = suF + h->n_units;
+  int* sI = reinterpret_cast<int*>(suT + h->n_units);
+  const size_t bl = sizeof(double) * h->n_lat, bu = sizeof(double) * h->n_units;
+  if (F) GF_CK(h, cudaMemcpyAsync(sF, h->d_lF, bl, cudaMemcpyDeviceToHost, h->stream));
+  if (theta) GF_CK(h, cudaMemcpyAsync(sT, h->d_lT, bl, cudaMemcpyDeviceToHost, h->stream));
+  if (uF) GF_CK(h, cudaMemcpyAsync(suF, h->d_uF, bu, cudaMemcpyDeviceToHost, h->stream));
+  if (uT) GF_CK(h, cudaMemcpyAsync(suT, h->d_uT, bu, cudaMemcpyDeviceToHost, h->stream));
+  if (iters) GF_CK(h, cudaMemcpyAsync(sI, h->d_iters, sizeof(int) * h->n_units, cudaMemcpyDeviceToHost, h->stream));
   GF_CK(h, cudaStreamSynchronize(h->stream));
+  if (F) std::memcpy(F, sF, bl);
+  if (theta) std::memcpy(theta, sT, bl);
+  if (uF) std::memcpy(uF, suF, bu);
+  if (uT) std::memcpy(uT, suT, bu);
+  if (iters) std::memcpy(iters, sI, sizeof(int) * h->n_units);
   return GF_OK;
 }
 
@@ -1065,6 +1079,12 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
     h->st_host = nullptr;
     return bail(GF_ENOMEM, "pinned host memory for the loop state");
   }
+  if (cudaHostAlloc((void**)&h->out_host, sizeof(double) * (2 * (size_t)n_lat + 2 * (size_t)h->L.n_units) +
+                                              sizeof(int) * (size_t)h->L.n_units,
+                    cudaHostAllocDefault) != cudaSuccess) {
+    h->out_host = nullptr;
+    return bail(GF_ENOMEM, "pinned host memory for the results");
+  }
   for (auto& ev : h->st_ev)
     if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
       ev = nullptr;
@@ -1182,6 +1202,7 @@ void gf_destroy(gf_handle* h) {
   for (auto& ev : h->st_ev)
     if (ev) cudaEventDestroy(ev);
   if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->out_host) cudaFreeHost(h->out_host);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;
 }

@@ -112,6 +112,23 @@ __host__ __device__ inline bool state_reunit_sweep(const DevState* st) {
 }
 
 // ----------------------------------------------------------------------------------
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialization (launch_dep) may be scheduled while the kernel before it in the stream
+// is still running.  grid_dep_wait() returns once that kernel has completed and its
+// memory operations are visible.  Every block of such a kernel calls it first, before
+// any memory access and before any early return: a block that left without waiting
+// could let the kernel complete ahead of its predecessor, and the next kernel's wait
+// would then no longer cover the predecessor's writes.  grid_dep_launch() lets the next
+// kernel of the stream be scheduled once every block of this one has started; its
+// blocks take the resources this kernel's blocks free and wait in grid_dep_wait().
+// Both are no-ops in a kernel launched without the attribute.
+// ----------------------------------------------------------------------------------
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+// ----------------------------------------------------------------------------------
 // Complex arithmetic in a fixed order
 // ----------------------------------------------------------------------------------
 template <class T>

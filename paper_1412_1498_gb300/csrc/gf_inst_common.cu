@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   __shared__ float2 red[3][kFinishThreads];
   __shared__ int s_last;
   __shared__ int s_cnt[kFinishThreads / 32];
+  grid_dep_wait();
+  grid_dep_launch();
   const int tid = (int)threadIdx.x;
   const int u = (int)blockIdx.x;
   const bool loop = a.mode == FINISH_LOOP || a.mode == FINISH_ODD;
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
 }
 
 void launch_finish(const FinishArgs& a, cudaStream_t s) {
-  k_finish<<<a.n_units, kFinishThreads, 0, s>>>(a);
+  launch_dep(k_finish, dim3(a.n_units), dim3(kFinishThreads), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------------

@@ -539,6 +539,26 @@ __global__ void k_to_fp64(const char* src, char* dst, LatDev lat_src, LatDev lat
 // ----------------------------------------------------------------------------------
 // Host-side launchers (defined in the instantiation units)
 // ----------------------------------------------------------------------------------
+// A kernel launch with programmatic stream serialization: the kernel (which calls
+// grid_dep_wait() first in every block) may be scheduled while the previous kernel of
+// the stream runs, so its launch latency and block start-up overlap that kernel's tail.
+// Captured into a graph, the launch becomes a programmatic dependency edge.
+template <typename... P, typename... A>
+inline cudaError_t launch_dep(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A... args) {
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 void launch_sweep(int storage, int nd, bool repro, int variant, const SweepArgs& a, int n_tiles,
                   int threads, cudaStream_t s);
 void launch_measure(int storage, int nd, int variant, const MeasureArgs& a, int n_tiles, int threads,

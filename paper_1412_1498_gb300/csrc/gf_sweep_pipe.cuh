@@ -79,6 +79,8 @@ template <int ND, int FORM>
 __global__ void __launch_bounds__(256) k_or_sweep_pipe(SweepArgs a) {
   extern __shared__ float4 sm[];
   __shared__ double red[2][64];  // alternate per tile sum: no barrier after the sum
+  grid_dep_wait();
+  grid_dep_launch();
   int rb = 0;
   bool reunit_now = a.reunit != 0, measure_now = a.measure != 0;
   if (a.st) {
@@ -223,6 +225,8 @@ template <int ND>
 __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
   extern __shared__ float4 sm[];
   __shared__ double red[2][64];  // alternate per tile sum, as in k_or_sweep_pipe
+  grid_dep_wait();
+  grid_dep_launch();
   int rb = 0;
   if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact || !a.st->hold)) return;
   int k = blockIdx.x;
