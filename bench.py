@@ -418,8 +418,9 @@ def run_gpu(args):
     bytes_per_step = STEP_BYTES + CHECK_BYTES / args.steps
     ms_total, value = reduce_over_ranks(ms_total, args.steps, world, bytes_per_step, dist, dev)
     ms_step = ms_total / args.steps
-    # our kernels launched in the timed gf_fix: the opening measurement (two F/theta
-    # passes and a finish), then per replayed graph three per captured sweep (even and
+    # our kernels launched in the timed gf_fix: the opening check (the odd-site F/theta
+    # pass and its finish, then the even-site pass and a reset, which find nothing to do
+    # when the odd part decides), then per replayed graph three per captured sweep (even and
     # odd half-sweep, the odd-part finish) and the even-site pass with the loop finish
     # that close the graph (they work on the budget's last sweep only: every other sweep
     # is decided by its odd part here); the library picks the graph lengths (16, 8, 4,
@@ -434,7 +435,7 @@ def run_gpu(args):
         captured += 16 >> k
         replays += 1
         left -= 16 >> k
-    launches = 3 + captured * 3 + 2 * replays
+    launches = 4 + captured * 3 + 2 * replays
 
     # ---- end to end through the C ABI with pinned host buffers: upload, one step, download
     Uh = torch.from_numpy(U).pin_memory()

@@ -496,6 +496,32 @@ int enqueue_measure_all(gf_handle* h, int mode) {
   return GF_OK;
 }
 
+// The opening check of a phase (Algorithm 1 stops before its first sweep when theta <
+// eps): the odd-site pass (F and the odd-site part of theta), then FINISH_OPEN, which
+// starts every unit whose odd part alone reaches its threshold (theta >= its odd part,
+// so the full theta decides the same).  Only if some unit is undecided (or a history is
+// kept) do the even-site pass and a reset run, gated on the loop state; they measure
+// every unit with the same sums as enqueue_measure_all.  The odd pass walks the tiles
+// backwards so that the first even half-sweep starts where it ended.
+int enqueue_opening(gf_handle* h) {
+  const int st = cur_storage(h);
+  MeasureArgs mo = measure_args(h, 1, false, 1);
+  mo.part_F = h->d_partF;
+  launch_measure(st, h->nd, h->variant, mo, h->n_tiles, h->threads, h->stream);
+  GF_CK_LAUNCH(h);
+  launch_finish(finish_args(h, FINISH_OPEN), h->stream);
+  GF_CK_LAUNCH(h);
+  MeasureArgs me = measure_args(h, 0, false, 0);
+  me.st = h->d_state;
+  launch_measure(st, h->nd, h->variant, me, h->n_tiles, h->threads, h->stream);
+  GF_CK_LAUNCH(h);
+  FinishArgs fr = finish_args(h, FINISH_RESET);
+  fr.gated = 1;
+  launch_finish(fr, h->stream);
+  GF_CK_LAUNCH(h);
+  return GF_OK;
+}
+
 // One sweep of the device-driven loop: even half-sweep, odd half-sweep (F and odd-site
 // theta fused on check sweeps), FINISH_ODD, which decides every unit whose odd part alone
 // settles the stop (theta >= its odd part) and closes the sweep.  When some unit is
@@ -614,7 +640,7 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   s.hist_n = h->hist_n;
   s.hist_base = h->hist_sweeps - offset;
   GF_CK(h, cudaMemcpyAsync(h->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream));
-  int rc = enqueue_measure_all(h, FINISH_RESET);
+  int rc = budget == 0 ? enqueue_measure_all(h, FINISH_RESET) : enqueue_opening(h);
   if (rc != GF_OK) return rc;
   if ((rc = ensure_graphs(h)) != GF_OK) return rc;
   int planned = 0, inflight = 0, w = 0, r = 0, drained_at = -1;

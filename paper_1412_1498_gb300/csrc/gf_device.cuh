@@ -75,6 +75,7 @@ struct DevState {
   unsigned int ticket;  // last-block-done counter of the finishing kernel
   int stop;             // Fourier-accelerated loop: final field measured, nothing left to do
   int need_exact;       // this check sweep has units whose odd-site theta alone is below eps
+                        // (2: the opening check of a phase has such units)
   int sweep_closed;     // the odd-part finish already counted this sweep (nothing pending)
   int hold;             // the odd-part finish left this sweep open: it waits for the even-site
                         // pass and the loop finish, and no sweep starts before they ran
@@ -109,6 +110,13 @@ __host__ __device__ inline bool state_check_sweep(const DevState* st) {
 }
 __host__ __device__ inline bool state_reunit_sweep(const DevState* st) {
   return st->reunit_interval > 0 && ((st->sweep + 1) % st->reunit_interval) == 0;
+}
+// the gated even-site theta pass runs: a check sweep of the loop, or the opening check of
+// a phase, was left open for units that the odd-site part alone does not decide
+__host__ __device__ inline bool state_even_pass(const DevState* st) {
+  if (!st->hold) return false;
+  if (st->need_exact == 2) return true;
+  return st->need_exact && state_running(st) && state_check_sweep(st);
 }
 
 // ----------------------------------------------------------------------------------

@@ -18,7 +18,11 @@ namespace gf {
 // last sweep of the budget) are pending.  With nothing pending ODD also does the
 // sweep's bookkeeping and closes it; otherwise the even-site pass runs for the pending
 // units and LOOP completes their theta and masks, counts the sweep and updates the
-// loop state.
+// loop state.  OPEN is the opening check of a phase in the same manner: after the
+// odd-site pass alone it starts every unit whose odd part is >= its threshold; if some
+// unit is undecided it leaves the loop state open (hold, need_exact = 2), and the gated
+// even-site pass and a gated RESET then measure every unit as RESET does.
+//
 // One history record: the sweep number, then F and theta of every lattice (lattice totals
 // already written); by one thread.
 __device__ __forceinline__ void history_record(const FinishArgs& a, int sweep_no) {
@@ -46,6 +50,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   // kernel is short and its time is mostly dependent round trips to memory.
   const int n_active = a.st->n_active, sweep = a.st->sweep, limit = a.st->limit;
   const int ci = a.st->check_interval, closed = a.st->sweep_closed, hold = a.st->hold;
+  const int need_in = a.st->need_exact;
   const double eps = a.st->eps, eps_mid = a.st->eps_mid;
   const int final_level = a.st->final_level;
   const int lvl_in = a.active[u];  // > 0: sweeping at that precision level
@@ -58,7 +63,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   // mostly has nothing to add, loads inside the reduction.)
   const bool outside = a.mode == FINISH_MEASURE || a.mode == FINISH_RESET || a.mode == FINISH_ENTER;
   const bool early = a.mode != FINISH_LOOP;
-  const float2* p1 = a.mode == FINISH_ODD ? a.part_th_odd : a.part_th_even;
+  const float2* p1 = (a.mode == FINISH_ODD || a.mode == FINISH_OPEN) ? a.part_th_odd : a.part_th_even;
   float2 x0[kFinishUnroll], x1[kFinishUnroll], x2[kFinishUnroll];
 #pragma unroll
   for (int j = 0; j < kFinishUnroll; ++j) {
@@ -86,6 +91,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
     // second one after the sweep was resolved does nothing
     if (a.mode == FINISH_LOOP && (closed || !hold)) return;
   }
+  if (a.gated && !(hold && need_in == 2)) return;  // the opening check decided every unit
   bool reduce;
   // a sweep without a check is closed by the odd-part finish (counts, no sums)
   if (a.mode == FINISH_ODD) reduce = was_active && check;
@@ -142,9 +148,19 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
     int pend = 0;
     bool act = was_active;
     // the unit's precision level (a reset starts every unit at level 1) and its threshold
-    const int lvl = a.mode == FINISH_RESET ? 1 : lvl_in;
+    const int lvl = (a.mode == FINISH_RESET || a.mode == FINISH_OPEN) ? 1 : lvl_in;
     const double thr = (lvl == 1 && final_level > 1) ? eps_mid : eps;
-    if (a.mode == FINISH_ODD) {
+    if (a.mode == FINISH_OPEN) {
+      // F and the odd-site part of theta (kept until a check replaces them); the unit
+      // sweeps if that part alone reaches the threshold, otherwise it is undecided
+      a.unit_sumF[u] = s0;
+      a.unit_F[u] = s0 * invF;
+      a.unit_sumTh[u] = s1;
+      a.unit_theta[u] = s1 * invT;
+      pend = a.hist != nullptr || !(s1 * invT >= thr);  // a history wants the opening theta
+      a.pending[u] = pend ? 1 : 0;
+      if (!pend) a.active[u] = 1;
+    } else if (a.mode == FINISH_ODD) {
       if (reduce) {
         uF = s0;
         a.unit_sumF[u] = s0;
@@ -178,6 +194,13 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
         a.st->need_exact = 1;
         a.st->sweep_closed = 0;
         a.st->hold = 1;
+      } else if (a.mode == FINISH_OPEN) {
+        if (pend) {
+          a.st->need_exact = 2;
+          a.st->hold = 1;
+        } else {
+          a.st->n_active = 1;
+        }
       } else {
         if (a.mode == FINISH_ODD && was_active) a.iters[u] += 1;
         if (!loop || check) {
@@ -191,6 +214,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
           a.st->n_active = act ? 1 : 0;
         }
         if (a.mode == FINISH_LOOP) a.st->hold = 0;
+        if (a.gated) {
+          a.st->hold = 0;
+          a.st->need_exact = 0;
+        }
         if (loop) a.st->sweep = sweep + 1;
         if (a.hist && ((a.mode == FINISH_LOOP && check) || (a.mode == FINISH_RESET && a.st->hist_n == 0)))
           history_record(a, a.mode == FINISH_LOOP ? a.st->hist_base + sweep + 1 : 0);
@@ -206,9 +233,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   if (!s_last) return;
   __threadfence();
   // the loop state: counts, lattice totals in a fixed order
-  int cnt = 0;  // ODD: pending units; otherwise: active units
+  int cnt = 0;  // ODD, OPEN: pending units; otherwise: active units
   for (int v = tid; v < a.n_units; v += blockDim.x)
-    cnt += a.mode == FINISH_ODD ? (__ldcg(a.pending + v) != 0) : (__ldcg(a.active + v) > 0);
+    cnt += (a.mode == FINISH_ODD || a.mode == FINISH_OPEN) ? (__ldcg(a.pending + v) != 0)
+                                                           : (__ldcg(a.active + v) > 0);
   cnt = __reduce_add_sync(0xffffffffu, cnt);
   if ((tid & 31) == 0) s_cnt[tid >> 5] = cnt;
   __syncthreads();
@@ -219,6 +247,18 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
       a.st->need_exact = 1;
       a.st->sweep_closed = 0;
       a.st->hold = 1;
+      a.st->ticket = 0u;
+    }
+    return;
+  }
+  if (a.mode == FINISH_OPEN) {  // undecided units wait for the gated reset; else all sweep
+    if (tid == 0) {
+      if (n > 0) {
+        a.st->need_exact = 2;
+        a.st->hold = 1;
+      } else {
+        a.st->n_active = a.n_units;
+      }
       a.st->ticket = 0u;
     }
     return;
@@ -248,6 +288,10 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
       a.st->n_active = n;
     }
     if (a.mode == FINISH_LOOP) a.st->hold = 0;
+    if (a.gated) {
+      a.st->hold = 0;
+      a.st->need_exact = 0;
+    }
     if (a.hist && ((a.mode == FINISH_LOOP && check) || (a.mode == FINISH_RESET && a.st->hist_n == 0)))
       history_record(a, a.mode == FINISH_LOOP ? a.st->hist_base + sweep + 1 : 0);
     if (loop) a.st->sweep += 1;

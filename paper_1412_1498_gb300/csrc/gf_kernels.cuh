@@ -278,10 +278,12 @@ struct FinishArgs {
   int n_units;
   int n_lat;
   int nd;
-  int mode;                // FINISH_LOOP, FINISH_MEASURE, FINISH_RESET, FINISH_ODD, FINISH_ENTER
+  int mode;                // FINISH_LOOP, FINISH_MEASURE, FINISH_RESET, FINISH_ODD, FINISH_ENTER,
+                           // FINISH_OPEN
+  int gated;               // FINISH_RESET after FINISH_OPEN: runs only if that left units undecided
 };
 
-enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2, FINISH_ODD = 3, FINISH_ENTER = 4 };
+enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2, FINISH_ODD = 3, FINISH_ENTER = 4, FINISH_OPEN = 5 };
 
 // Fourier-accelerated steepest descent (kernels in gf_fasd.cuh)
 struct FasdArgs {
@@ -463,7 +465,7 @@ __global__ void __launch_bounds__(256) k_measure(MeasureArgs a) {
   using T = typename St::T;
   constexpr int NE = St::NE;
   __shared__ double red[64];
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact || !a.st->hold)) return;
+  if (a.st && !state_even_pass(a.st)) return;
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
   if (a.active && a.active[tile.w] != a.level) return;

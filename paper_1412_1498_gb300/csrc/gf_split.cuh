@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(256) k_or_sweep_split(SweepArgs a) {
 template <int ND>
 __global__ void __launch_bounds__(256) k_measure_split(MeasureArgs a) {
   __shared__ double red[64];
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact || !a.st->hold)) return;
+  if (a.st && !state_even_pass(a.st)) return;
   const int ti = a.reverse ? a.n_tiles - 1 - (int)blockIdx.x : (int)blockIdx.x;
   const int4 tile = a.tiles[ti];
   if (a.active && a.active[tile.w] != a.level) return;

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_measure_pipe(MeasureArgs a) {
   grid_dep_wait();
   grid_dep_launch();
   int rb = 0;
-  if (a.st && (!state_running(a.st) || !state_check_sweep(a.st) || !a.st->need_exact || !a.st->hold)) return;
+  if (a.st && !state_even_pass(a.st)) return;
   int k = blockIdx.x;
   if (k >= a.n_tiles) return;
   const int B = blockDim.x;

@@ -351,6 +351,44 @@ def test_edge_cases(gf):
     fx.close()
 
 
+@pytest.mark.parametrize("storage", [0, 2])
+def test_opening_check(gf, storage):
+    # gf_fix opens with the odd-site pass alone and starts every unit whose odd part of
+    # theta already reaches eps (theta >= its odd part); the even-site pass and a full
+    # reset run only when some unit is undecided.  (a) A lattice below eps at the
+    # opening: no sweep, F and theta exactly as gf_functional_theta gives them.  (b)
+    # Coulomb slices of which half are below eps at the opening (a smooth field with a
+    # Haar gauge transformation on the slices t < 4 only): per-slice iteration counts
+    # as the oracle's, and in FP64 the oracle's field.
+    dims = (6, 4, 6, 8)
+    U = fields.smooth_field(dims, 0.002, 91)
+    g = fields.gauge_field(dims, 92)
+    g[4:] = np.eye(3)
+    V = fields.gauge_transform(U, g)
+    fx = make(gf, dims, gf.GF_LANDAU, storage, repro=storage == gf.GF_FP64_18)
+    fx.upload(V)
+    F0, th0, _, _ = fx.functional_theta()
+    out = fx.fix(2.0 * th0[0], 10)
+    assert out["rc"] == gf.GF_OK and out["iters"][0] == 0
+    assert out["F"][0] == F0[0] and out["theta"][0] == th0[0]
+    fx.close()
+    fc = make(gf, dims, gf.GF_COULOMB, storage, repro=storage == gf.GF_FP64_18)
+    fc.upload(V)
+    ref = V.copy()
+    r = oracle.fix(ref, 1e-3, 500, 1.7, oracle.COULOMB)
+    assert list(r["slice_iters"][4:]) == [0, 0, 0, 0] and min(r["slice_iters"][:4]) > 0
+    out = fc.fix(1e-3, 500)
+    assert out["rc"] == gf.GF_OK
+    if storage == gf.GF_FP64_18:
+        assert np.array_equal(out["iters"], r["slice_iters"])
+        assert np.array_equal(fc.download(), ref)
+        assert abs(out["theta"][0] - r["theta"]) <= 1e-12 * r["theta"]
+    else:
+        assert list(out["iters"][4:]) == [0, 0, 0, 0]
+        assert np.abs(out["iters"][:4] - r["slice_iters"][:4]).max() <= 2
+    fc.close()
+
+
 @pytest.mark.parametrize("threads", [64, 128, 256])
 def test_block_sizes_agree(gf, threads):
     U = fields.random_gauge_config(DIMS, 0.5, 71)
