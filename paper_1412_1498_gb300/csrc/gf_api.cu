@@ -174,7 +174,6 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->unit_tiles = take(sizeof(int) * (n_units + 1));
   L->unit_lat = take(sizeof(int) * n_units);
   L->active = take(sizeof(int) * n_units);
-  L->iters = take(sizeof(int) * n_units);
   L->partF = take(sizeof(float2) * max_tiles);
   L->pthe = take(sizeof(float2) * max_tiles);
   L->ptho = take(sizeof(float2) * max_tiles);
@@ -185,6 +184,8 @@ bool plan(int n_lat, const int* dims, int gauge, int storage, int flags, Layout*
   L->usT = take(sizeof(double) * n_units);
   L->uF = take(sizeof(double) * n_units);
   L->uT = take(sizeof(double) * n_units);
+  // the result block, contiguous: iteration counts, lattice F and theta, loop state
+  L->iters = take(sizeof(int) * n_units);
   L->lF = take(sizeof(double) * n_lat);
   L->lT = take(sizeof(double) * n_lat);
   L->state = take(sizeof(DevState));
@@ -321,8 +322,12 @@ struct gf_handle {
   cudaGraphExec_t graph[3][5] = {};
   cudaGraphExec_t graph_mix[8] = {};
   cudaGraphExec_t graph_fasd = nullptr;
-  // loop-state snapshots of the replays in flight (pinned host ring) and their events
-  DevState* st_host = nullptr;
+  // pinned host ring: slots 0 and 1 receive the result block (iteration counts, lattice
+  // F and theta, loop state) behind each replay in flight, whose events follow the
+  // copies; slot 2 holds the loop state uploaded at the start of a phase
+  char* res_host = nullptr;
+  size_t res_bytes = 0, res_stride = 0;
+  int res_slot = -1;  // slot with the results of the loop that just ended, else -1
   cudaEvent_t st_ev[2] = {nullptr, nullptr};
   char* out_host = nullptr;  // pinned staging of the values gf_fix / gf_functional_theta return
   int last_active = 0;  // active units when the last OR loop (run_phase / run_mixed) ended
@@ -612,16 +617,25 @@ int graph_index(int left) {
   return k;
 }
 
+// The loop state, through the pinned upload slot of the result ring (stream-ordered after
+// any upload from it).
 int read_state(gf_handle* h, DevState* out) {
-  GF_CK(h, cudaMemcpyAsync(out, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  char* slot = h->res_host + 2 * h->res_stride;
+  GF_CK(h, cudaMemcpyAsync(slot, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
   GF_CK(h, cudaStreamSynchronize(h->stream));
+  std::memcpy(out, slot, sizeof(DevState));
   return GF_OK;
+}
+
+DevState* res_state(gf_handle* h, int slot) {
+  return reinterpret_cast<DevState*>(h->res_host + slot * h->res_stride + (h->L.state - h->L.iters));
 }
 
 // One phase of Algorithm 1 on the current buffer: measure, then sweeps until every
 // unit is below eps or `budget` sweeps were done.  *done receives the sweeps done.
-// Two graph replays are kept in flight: each one's loop state is copied to a pinned
-// host slot behind it, and the host reads a replay's state while the next one runs; the
+// Two graph replays are kept in flight: each one's result block (loop state, iteration
+// counts, lattice F and theta) is copied to a pinned host slot behind it, and the host
+// reads a replay's state while the next one runs; the
 // replay after the one that ends the run (every unit below eps) finds nothing to do.
 // Replays are planned as if all their sweeps ran; a sweep left open idles the rest of
 // its replay, so whenever nothing is in flight the plan restarts from the sweeps done.
@@ -639,17 +653,23 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
   s.final_level = 1;
   s.hist_n = h->hist_n;
   s.hist_base = h->hist_sweeps - offset;
-  GF_CK(h, cudaMemcpyAsync(h->d_state, &s, sizeof s, cudaMemcpyHostToDevice, h->stream));
+  h->res_slot = -1;
+  // from pinned memory: no staging copy on the host (the previous upload from this slot
+  // completed before the previous phase read any replay)
+  std::memcpy(h->res_host + 2 * h->res_stride, &s, sizeof s);
+  GF_CK(h, cudaMemcpyAsync(h->d_state, h->res_host + 2 * h->res_stride, sizeof s, cudaMemcpyHostToDevice,
+                           h->stream));
   int rc = budget == 0 ? enqueue_measure_all(h, FINISH_RESET) : enqueue_opening(h);
   if (rc != GF_OK) return rc;
   if ((rc = ensure_graphs(h)) != GF_OK) return rc;
-  int planned = 0, inflight = 0, w = 0, r = 0, drained_at = -1;
+  int planned = 0, inflight = 0, w = 0, r = 0, drained_at = -1, last = -1;
   bool stop = budget == 0;
   for (;;) {
     while (!stop && inflight < 2 && planned < budget) {
       const int k = graph_index(budget - planned);
       GF_CK(h, cudaGraphLaunch(h->graph[h->cur][k], h->stream));
-      GF_CK(h, cudaMemcpyAsync(h->st_host + w, h->d_state, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+      GF_CK(h, cudaMemcpyAsync(h->res_host + w * h->res_stride, h->ws + h->L.iters, h->res_bytes,
+                               cudaMemcpyDeviceToHost, h->stream));
       GF_CK(h, cudaEventRecord(h->st_ev[w], h->stream));
       planned += kGraphSweeps >> k;
       w ^= 1;
@@ -657,7 +677,8 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
     }
     if (inflight == 0) break;
     GF_CK(h, cudaEventSynchronize(h->st_ev[r]));
-    s = h->st_host[r];
+    s = *res_state(h, r);
+    last = r;
     r ^= 1;
     --inflight;
     if (s.n_active == 0 || s.sweep >= s.limit) stop = true;
@@ -669,16 +690,21 @@ int run_phase(gf_handle* h, double eps, int budget, int* done) {
       planned = s.sweep - offset;
     }
   }
+  // the last replay read is the last work of the phase: its slot holds the results
+  int slot = last;
   if (budget == 0 || planned == 0) {
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
+    slot = -1;
   }
   if (s.hold) {  // not expected: every replay ends with its open sweep resolved
     if ((rc = resolve_open_sweep(h)) != GF_OK) return rc;
     if ((rc = read_state(h, &s)) != GF_OK) return rc;
+    slot = -1;
   }
   *done = s.sweep - offset;
   h->hist_n = s.hist_n;
   h->last_active = s.n_active;
+  h->res_slot = slot;
   return GF_OK;
 }
 
@@ -916,9 +942,20 @@ int run_mixed(gf_handle* h, double eps, int budget, int* sweeps_fp32, int* sweep
   return GF_OK;
 }
 
-// The requested results through the handle's pinned staging: asynchronous copies and one
-// synchronisation (a copy into pageable memory would block on each call).
+// The requested results: from the result block that the loop which just ended copied
+// behind its last replay (lattice totals and iteration counts), else through the
+// handle's pinned staging with asynchronous copies and one synchronisation (a copy into
+// pageable memory would block on each call).
 int copy_out(gf_handle* h, double* F, double* theta, double* uF, double* uT, int* iters) {
+  const int slot = h->res_slot;
+  h->res_slot = -1;
+  if (slot >= 0 && !uF && !uT) {
+    const char* b = h->res_host + slot * h->res_stride;
+    if (iters) std::memcpy(iters, b, sizeof(int) * h->n_units);
+    if (F) std::memcpy(F, b + (h->L.lF - h->L.iters), sizeof(double) * h->n_lat);
+    if (theta) std::memcpy(theta, b + (h->L.lT - h->L.iters), sizeof(double) * h->n_lat);
+    return GF_OK;
+  }
   double* sF = reinterpret_cast<double*>(h->out_host);
   double* sT = sF + h->n_lat;
   double* suF = sT + h->n_lat;
@@ -1101,8 +1138,10 @@ int gf_create_batch(int n_lat, const int* dims, int gauge, int storage, int flag
   }
   if (cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
     return bail(GF_ECUDA, "cudaStreamCreate failed");
-  if (cudaHostAlloc((void**)&h->st_host, 2 * sizeof(DevState), cudaHostAllocDefault) != cudaSuccess) {
-    h->st_host = nullptr;
+  h->res_bytes = h->L.state + sizeof(DevState) - h->L.iters;
+  h->res_stride = align_up(h->res_bytes);
+  if (cudaHostAlloc((void**)&h->res_host, 3 * h->res_stride, cudaHostAllocDefault) != cudaSuccess) {
+    h->res_host = nullptr;
     return bail(GF_ENOMEM, "pinned host memory for the loop state");
   }
   if (cudaHostAlloc((void**)&h->out_host, sizeof(double) * (2 * (size_t)n_lat + 2 * (size_t)h->L.n_units) +
@@ -1227,7 +1266,7 @@ void gf_destroy(gf_handle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   for (auto& ev : h->st_ev)
     if (ev) cudaEventDestroy(ev);
-  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->res_host) cudaFreeHost(h->res_host);
   if (h->out_host) cudaFreeHost(h->out_host);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;
