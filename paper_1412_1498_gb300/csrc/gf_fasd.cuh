@@ -137,48 +137,38 @@ __device__ __forceinline__ void fft_line_reg(cx<T>* d, int estride, int sign) {
   for (int r = 0; r < L; ++r) d[bit_rev(r, LOGL) * estride] = v[r];
 }
 
-// decimation in time on registers: bit-reversed order in, natural order out
-template <class T, int LOGL>
-__device__ __forceinline__ void dit_reg(cx<T> (&v)[1 << LOGL], int sign) {
-  constexpr int L = 1 << LOGL;
-#pragma unroll
-  for (int span = 1; span < L; span <<= 1) {
-#pragma unroll
-    for (int s = 0; s < L; s += 2 * span) {
-#pragma unroll
-      for (int j = 0; j < span; ++j) {
-        const cx<T> a = v[s + j];
-        cx<T> b = v[s + j + span];
-        if (j != 0) b = cmul(b, twiddle<T, L>(j * (L / (2 * span)), sign));  // exp(-2 pi i j / (2 span))
-        v[s + j] = cadd(a, b);
-        v[s + j + span] = csub(a, b);
-      }
-    }
-  }
-}
-
 __device__ __forceinline__ float filter_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double filter_div(double a, double b) { return a / b; }
 
-// The last transform direction of a line, the Fourier filter and the inverse in one
-// pass: forward transform by decimation in frequency (modes in bit-reversed order), each
-// mode k scaled in place by coef / (base + s2[k]) (0 where that is not positive: the
-// zero mode), inverse transform by decimation in time (bit-reversed in, natural out).
+// One line of the z/t stage through registers, with a single copy of the transform
+// code for every pass: the inverse transform is the forward one of the conjugate,
+// conjugated (sum_k x_k exp(+2 pi i j k / L) = conj(sum_k conj(x_k) exp(-2 pi i j k /
+// L))), so each pass is load (conjugated for kind 3), decimation in frequency, store in
+// natural order: kind 0 forward; kind 1 forward, then each mode k scaled by coef / (base
+// + s2[k]) (0 where that is not positive: the zero mode) and stored conjugated; kind 2
+// the inverse of what kind 1 stored; kind 3 inverse.  A straight-line sequence of both
+// directions (and the filter between them in registers) was too long for the
+// instruction caches; one transform per pass keeps the stage's code small.
 template <class T, int LOGL>
-__device__ __forceinline__ void filter_line_reg(cx<T>* d, int estride, T base, const T* s2, T coef) {
+__device__ __forceinline__ void zt_line(cx<T>* d, int es, int kind, T base, const T* s2, T coef) {
   constexpr int L = 1 << LOGL;
   cx<T> v[L];
+  const bool conj_in = kind == 3, conj_out = kind != 0;
 #pragma unroll
-  for (int k = 0; k < L; ++k) v[k] = d[k * estride];
-  dif_reg<T, LOGL>(v, -1);
-#pragma unroll
-  for (int r = 0; r < L; ++r) {
-    const T p2 = base + s2[bit_rev(r, LOGL)];
-    v[r] = cscale(v[r], p2 > T(0) ? filter_div(coef, p2) : T(0));
+  for (int k = 0; k < L; ++k) {
+    const cx<T> x = d[k * es];
+    v[k] = {x.re, conj_in ? -x.im : x.im};
   }
-  dit_reg<T, LOGL>(v, +1);
+  dif_reg<T, LOGL>(v, -1);
+  if (kind == 1) {
 #pragma unroll
-  for (int k = 0; k < L; ++k) d[k * estride] = v[k];
+    for (int r = 0; r < L; ++r) {  // v[r] holds mode bit_rev(r)
+      const T p2 = base + s2[bit_rev(r, LOGL)];
+      v[r] = cscale(v[r], p2 > T(0) ? filter_div(coef, p2) : T(0));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < L; ++r) d[bit_rev(r, LOGL) * es] = {v[r].re, conj_out ? -v[r].im : v[r].im};
 }
 
 template <class T>
@@ -564,31 +554,32 @@ __global__ void __launch_bounds__(kFasdThreads, 2) k_fasd_zt(FasdArgs a) {
     cx<T>* col = buf[cur];
     const T pxy = s2y[ky];
     if (lf <= 5 && lz <= 5) {
-      // lines through registers; the last direction is transformed, filtered and
-      // transformed back in one pass (filter_line_reg)
-      if (ND == 4) {
-        fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, -1);  // along z
-        for (int l = threadIdx.x; l < Lz * KX; l += blockDim.x) {     // along t: line (kxl, kz)
-          const T base = s2x[kx0 + (l & mk)] + pxy + s2z[l >> lk];
-          switch (lf) {
-            case 1: filter_line_reg<T, 1>(col + l, pitch, base, s2t, coef); break;
-            case 2: filter_line_reg<T, 2>(col + l, pitch, base, s2t, coef); break;
-            case 3: filter_line_reg<T, 3>(col + l, pitch, base, s2t, coef); break;
-            case 4: filter_line_reg<T, 4>(col + l, pitch, base, s2t, coef); break;
-            default: filter_line_reg<T, 5>(col + l, pitch, base, s2t, coef); break;
+      // lines through registers (zt_line), one transform per pass: Landau z forward, t
+      // forward and filtered, t back, z back; Coulomb z forward and filtered, z back
+#pragma unroll 1
+      for (int ph = ND == 4 ? 0 : 1; ph < (ND == 4 ? 4 : 3); ++ph) {
+        const bool zl = ND == 4 && (ph == 0 || ph == 3);  // z lines (kxl, tl) of a Landau item
+        const int nl = zl ? nt * KX : (ND == 4 ? Lz * KX : KX);
+        const int lg = zl ? lz : lf;
+        for (int l = threadIdx.x; l < nl; l += blockDim.x) {
+          cx<T>* p = col + l;
+          int es = KX;
+          T base = T(0);
+          const T* s2 = ND == 4 ? s2t : s2z;
+          if (zl) {
+            p = col + (l & mk) + (l >> lk) * pitch;
+          } else if (ND == 4) {  // t line (kxl, kz)
+            es = pitch;
+            base = s2x[kx0 + (l & mk)] + pxy + s2z[l >> lk];
+          } else {  // z line kxl of the slice
+            base = s2x[kx0 + l] + pxy;
           }
-        }
-        __syncthreads();
-        fft_lines_reg(col, twz, nt * KX, lz, KX, 1, pitch, KX, +1);
-      } else {
-        for (int l = threadIdx.x; l < KX; l += blockDim.x) {  // along z: line kxl of the slice
-          const T base = s2x[kx0 + l] + pxy;
-          switch (lf) {
-            case 1: filter_line_reg<T, 1>(col + l, KX, base, s2z, coef); break;
-            case 2: filter_line_reg<T, 2>(col + l, KX, base, s2z, coef); break;
-            case 3: filter_line_reg<T, 3>(col + l, KX, base, s2z, coef); break;
-            case 4: filter_line_reg<T, 4>(col + l, KX, base, s2z, coef); break;
-            default: filter_line_reg<T, 5>(col + l, KX, base, s2z, coef); break;
+          switch (lg) {
+            case 1: zt_line<T, 1>(p, es, ph, base, s2, coef); break;
+            case 2: zt_line<T, 2>(p, es, ph, base, s2, coef); break;
+            case 3: zt_line<T, 3>(p, es, ph, base, s2, coef); break;
+            case 4: zt_line<T, 4>(p, es, ph, base, s2, coef); break;
+            default: zt_line<T, 5>(p, es, ph, base, s2, coef); break;
           }
         }
         __syncthreads();
