@@ -436,6 +436,7 @@ SweepArgs sweep_args(gf_handle* h, int parity, bool loop, int reverse) {
   a.reunit = 0;
   a.measure = 0;
   a.level = 1;
+  a.dep = h->n_units == 1;
   a.omega = h->omega;
   return a;
 }
@@ -455,6 +456,7 @@ MeasureArgs measure_args(gf_handle* h, int parity, bool loop, int reverse) {
   a.part_theta = parity == 0 ? h->d_pthe : h->d_ptho;
   a.parity = parity;
   a.level = 1;
+  a.dep = h->n_units == 1;
   return a;
 }
 
@@ -486,6 +488,7 @@ FinishArgs finish_args(gf_handle* h, int mode) {
   a.n_lat = h->n_lat;
   a.nd = h->nd;
   a.mode = mode;
+  a.dep = h->n_units == 1;
   return a;
 }
 

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
 }
 
 void launch_finish(const FinishArgs& a, cudaStream_t s) {
-  launch_dep(k_finish, dim3(a.n_units), dim3(kFinishThreads), 0, s, a);
+  launch_dep(a.dep != 0, k_finish, dim3(a.n_units), dim3(kFinishThreads), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------------

@@ -58,7 +58,7 @@ void launch_measure_fp32_pipe(int nd, const MeasureArgs& a, int n_tiles, int thr
   if (grid <= 0) grid = 1;
   if (grid > n_tiles) grid = n_tiles;
   const size_t smem = 2 * 6 * nd * threads * sizeof(float4);
-  launch_dep(nd == 4 ? k_measure_pipe<4> : k_measure_pipe<3>, dim3(grid), dim3(threads), smem, s, a);
+  launch_dep(a.dep != 0, nd == 4 ? k_measure_pipe<4> : k_measure_pipe<3>, dim3(grid), dim3(threads), smem, s, a);
 }
 
 // CTAs of the persistent pipelined sweep over n_tiles tiles (also the number of per-CTA
@@ -78,7 +78,7 @@ void launch_sweep_fp32_pipe(int nd, const SweepArgs& a, int n_tiles, int threads
   auto kern = a.form == GF_OR_FIRST_ORDER
                   ? (nd == 4 ? k_or_sweep_pipe<4, GF_OR_FIRST_ORDER> : k_or_sweep_pipe<3, GF_OR_FIRST_ORDER>)
                   : (nd == 4 ? k_or_sweep_pipe<4, GF_OR_EXACT> : k_or_sweep_pipe<3, GF_OR_EXACT>);
-  launch_dep(kern, dim3(grid), dim3(threads), smem, s, a);
+  launch_dep(a.dep != 0, kern, dim3(grid), dim3(threads), smem, s, a);
 }
 
 void launch_sweep_fp32(int storage, int nd, const SweepArgs& a, int n_tiles, int threads,

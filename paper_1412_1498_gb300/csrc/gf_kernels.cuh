@@ -230,6 +230,7 @@ struct SweepArgs {
   int level;               // precision level these tiles must carry in `active` (1 unless mixed)
   int cta_sums;            // persistent kernels, one unit: F and theta partials per CTA (indexed
                            // by blockIdx.x) instead of per tile
+  int dep;                 // launch with programmatic stream serialisation (launch_dep)
   double omega;
 };
 
@@ -245,6 +246,7 @@ struct MeasureArgs {
   int n_tiles;
   int reverse;
   int level;
+  int dep;                 // launch with programmatic stream serialisation (launch_dep)
 };
 
 constexpr int kFinishThreads = 256;  // threads of a finishing block (one block per unit)
@@ -281,6 +283,7 @@ struct FinishArgs {
   int mode;                // FINISH_LOOP, FINISH_MEASURE, FINISH_RESET, FINISH_ODD, FINISH_ENTER,
                            // FINISH_OPEN
   int gated;               // FINISH_RESET after FINISH_OPEN: runs only if that left units undecided
+  int dep;                 // launch with programmatic stream serialisation (launch_dep)
 };
 
 enum { FINISH_LOOP = 0, FINISH_MEASURE = 1, FINISH_RESET = 2, FINISH_ODD = 3, FINISH_ENTER = 4, FINISH_OPEN = 5 };
@@ -541,12 +544,15 @@ __global__ void k_to_fp64(const char* src, char* dst, LatDev lat_src, LatDev lat
 // ----------------------------------------------------------------------------------
 // Host-side launchers (defined in the instantiation units)
 // ----------------------------------------------------------------------------------
-// A kernel launch with programmatic stream serialization: the kernel (which calls
-// grid_dep_wait() first in every block) may be scheduled while the previous kernel of
-// the stream runs, so its launch latency and block start-up overlap that kernel's tail.
-// Captured into a graph, the launch becomes a programmatic dependency edge.
+// A kernel launch with programmatic stream serialization when `dep` is set: the kernel
+// (which calls grid_dep_wait() first in every block) may be scheduled while the previous
+// kernel of the stream runs, so its launch latency and block start-up overlap that
+// kernel's tail.  Captured into a graph, the launch becomes a programmatic dependency
+// edge.  The driver sets it for one-unit handles, whose loop it speeds up; the loops of
+// many units (five launches per sweep, a finishing block per unit) ran 3-4% slower with
+// it, and launch plainly.
 template <typename... P, typename... A>
-inline cudaError_t launch_dep(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+inline cudaError_t launch_dep(bool dep, void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                               A... args) {
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -557,7 +563,7 @@ inline cudaError_t launch_dep(void (*kern)(P...), dim3 grid, dim3 block, size_t 
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = dep ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
