@@ -299,8 +299,77 @@ __global__ void __launch_bounds__(kFinishThreads) k_finish(FinishArgs a) {
   }
 }
 
+// FINISH_ODD of a one-unit loop (the odd half-sweep's per-CTA partials, a few hundred)
+// by one warp: each lane adds every 32nd partial in order, then a fixed shuffle tree, no
+// block barrier; thread 0 then does exactly what k_finish's one-unit FINISH_ODD does.
+// This finish runs after every odd half-sweep, between it and the next even one.
+__global__ void __launch_bounds__(32) k_finish_odd1(FinishArgs a) {
+  grid_dep_wait();
+  grid_dep_launch();
+  const int lane = (int)threadIdx.x;
+  const int n_active = a.st->n_active, sweep = a.st->sweep, limit = a.st->limit;
+  const int ci = a.st->check_interval, hold = a.st->hold;
+  if (!(n_active > 0 && sweep < limit) || hold) return;  // stopped, or the sweep is open
+  const bool check = ((sweep + 1) % ci) == 0 || sweep + 1 == limit;  // state_check_sweep
+  const int lvl = a.active[0];
+  const bool was_active = lvl > 0;
+  const bool reduce = was_active && check;
+  float2 aF = make_float2(0.f, 0.f), aT = aF;
+  if (reduce) {
+#pragma unroll 4
+    for (int i = lane; i < a.n_odd_parts; i += 32) {
+      aF = pair_add(aF, a.part_F[i]);
+      aT = pair_add(aT, a.part_th_odd[i]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float2 bF, bT;
+      bF.x = __shfl_down_sync(0xffffffffu, aF.x, o);
+      bF.y = __shfl_down_sync(0xffffffffu, aF.y, o);
+      bT.x = __shfl_down_sync(0xffffffffu, aT.x, o);
+      bT.y = __shfl_down_sync(0xffffffffu, aT.y, o);
+      aF = pair_add(aF, bF);
+      aT = pair_add(aT, bT);
+    }
+  }
+  if (lane != 0) return;
+  const double invF = a.unit_norm[0], invT = a.unit_norm[1];
+  const double uF_old = a.unit_sumF[0], uT_old = a.unit_sumTh[0];
+  const double thr = (lvl == 1 && a.st->final_level > 1) ? a.st->eps_mid : a.st->eps;
+  const bool forced = sweep + 1 == limit;  // the budget's last sweep is measured exactly
+  double uF = uF_old;
+  bool pend = false;
+  if (reduce) {
+    const double s0 = pair_value(aF), s1 = pair_value(aT);
+    uF = s0;
+    a.unit_sumF[0] = s0;
+    a.unit_F[0] = s0 * invF;
+    a.unit_sumTh_odd[0] = s1;
+    pend = forced || a.hist != nullptr || !(s1 * invT >= thr);  // a history wants every theta
+  }
+  a.pending[0] = pend ? lvl : 0;
+  if (pend) {
+    a.st->need_exact = 1;
+    a.st->sweep_closed = 0;
+    a.st->hold = 1;
+  } else {
+    if (was_active) a.iters[0] += 1;
+    if (check) {
+      a.lat_F[0] = uF * invF;
+      a.lat_theta[0] = uT_old * invT;
+    }
+    a.st->need_exact = 0;
+    a.st->sweep_closed = 1;
+    a.st->sweep = sweep + 1;
+  }
+  a.st->ticket = 0u;
+}
+
 void launch_finish(const FinishArgs& a, cudaStream_t s) {
-  launch_dep(a.dep != 0, k_finish, dim3(a.n_units), dim3(kFinishThreads), 0, s, a);
+  if (a.mode == FINISH_ODD && a.n_units == 1 && a.n_odd_parts <= 1024)
+    launch_dep(a.dep != 0, k_finish_odd1, dim3(1), dim3(32), 0, s, a);
+  else
+    launch_dep(a.dep != 0, k_finish, dim3(a.n_units), dim3(kFinishThreads), 0, s, a);
 }
 
 // ---------------------------------------------------------------------------------
