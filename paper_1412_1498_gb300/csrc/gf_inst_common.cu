@@ -307,20 +307,26 @@ __global__ void __launch_bounds__(32) k_finish_odd1(FinishArgs a) {
   grid_dep_wait();
   grid_dep_launch();
   const int lane = (int)threadIdx.x;
+  // Every load is issued before anything depends on it (the partials too, although they
+  // are used only on check sweeps): the kernel is one round trip to L2, the tree and
+  // thread 0's stores.
   const int n_active = a.st->n_active, sweep = a.st->sweep, limit = a.st->limit;
-  const int ci = a.st->check_interval, hold = a.st->hold;
+  const int ci = a.st->check_interval, hold = a.st->hold, final_level = a.st->final_level;
+  const double eps = a.st->eps, eps_mid = a.st->eps_mid;
+  const int lvl = a.active[0];
+  const double invF = a.unit_norm[0], invT = a.unit_norm[1];
+  const double uF_old = a.unit_sumF[0], uT_old = a.unit_sumTh[0];
+  float2 aF = make_float2(0.f, 0.f), aT = aF;
+#pragma unroll 8
+  for (int i = lane; i < a.n_odd_parts; i += 32) {
+    aF = pair_add(aF, a.part_F[i]);
+    aT = pair_add(aT, a.part_th_odd[i]);
+  }
   if (!(n_active > 0 && sweep < limit) || hold) return;  // stopped, or the sweep is open
   const bool check = ((sweep + 1) % ci) == 0 || sweep + 1 == limit;  // state_check_sweep
-  const int lvl = a.active[0];
   const bool was_active = lvl > 0;
   const bool reduce = was_active && check;
-  float2 aF = make_float2(0.f, 0.f), aT = aF;
   if (reduce) {
-#pragma unroll 4
-    for (int i = lane; i < a.n_odd_parts; i += 32) {
-      aF = pair_add(aF, a.part_F[i]);
-      aT = pair_add(aT, a.part_th_odd[i]);
-    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       float2 bF, bT;
@@ -333,9 +339,7 @@ __global__ void __launch_bounds__(32) k_finish_odd1(FinishArgs a) {
     }
   }
   if (lane != 0) return;
-  const double invF = a.unit_norm[0], invT = a.unit_norm[1];
-  const double uF_old = a.unit_sumF[0], uT_old = a.unit_sumTh[0];
-  const double thr = (lvl == 1 && a.st->final_level > 1) ? a.st->eps_mid : a.st->eps;
+  const double thr = (lvl == 1 && final_level > 1) ? eps_mid : eps;
   const bool forced = sweep + 1 == limit;  // the budget's last sweep is measured exactly
   double uF = uF_old;
   bool pend = false;
