@@ -181,8 +181,11 @@ GF_API int gf_reunitarize(gf_handle *h);
  * odd-site part of theta inside the odd half-sweep; theta >= that part, so a unit whose
  * odd part alone reaches eps continues exactly as the full theta would decide, and the
  * even-site part is computed only for the other units and on the last sweep of the
- * budget.  F, theta and the masks at exit are exact (gf_set_history records theta at
- * every check).  FP32 storages take the odd-site values from K' = G K (K of Eq. (5)
+ * budget.  The measurement before the first sweep follows the same rule: the odd-site
+ * pass decides every unit whose odd part reaches eps, and the even-site pass runs only
+ * if some unit is undecided (a field already below eps returns the values
+ * gf_functional_theta gives).  F, theta and the masks at exit are exact
+ * (gf_set_history records theta at every check).  FP32 storages take the odd-site values from K' = G K (K of Eq. (5)
  * before the site's update, G its new transformation: Delta of the updated links is the
  * traceless anti-Hermitian part of K', Re Tr K' the site's share of Eq. (1)), i.e. of the
  * links before a reunitarisation in the same sweep, a difference at the rounding level;
