@@ -96,6 +96,27 @@ def reduce_over_ranks(ms_total: float, steps: int, world: int, bytes_per_step: i
     return ms_total, world * bytes_per_step * steps / (ms_total * 1e-3) / 1e9
 
 
+def timed_fix_launches(steps: int) -> int:
+    """Kernels a one-lattice gf_fix(eps, steps) launches when every sweep runs: the opening
+    check (the odd-site F/theta pass and its finish, then the even-site pass and a reset,
+    which find nothing to do when the odd part decides), then per replayed graph three per
+    captured sweep (even and odd half-sweep, the odd-part finish) and the even-site pass
+    with the loop finish that close the graph (they work on the budget's last sweep only:
+    every other sweep is decided by its odd part here).  The library picks the graph
+    lengths (16, 8, 4, 2 or 1 sweeps) from the sweeps left as below."""
+    captured, replays, left = 0, 0, steps
+    while left > 0:
+        k = 0
+        while k < 4 and (16 >> (k + 1)) >= left:
+            k += 1
+        if (16 >> k) - left > 2 and k < 4:
+            k += 1
+        captured += 16 >> k
+        replays += 1
+        left -= 16 >> k
+    return 4 + captured * 3 + 2 * replays
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -418,24 +439,7 @@ def run_gpu(args):
     bytes_per_step = STEP_BYTES + CHECK_BYTES / args.steps
     ms_total, value = reduce_over_ranks(ms_total, args.steps, world, bytes_per_step, dist, dev)
     ms_step = ms_total / args.steps
-    # our kernels launched in the timed gf_fix: the opening check (the odd-site F/theta
-    # pass and its finish, then the even-site pass and a reset, which find nothing to do
-    # when the odd part decides), then per replayed graph three per captured sweep (even and
-    # odd half-sweep, the odd-part finish) and the even-site pass with the loop finish
-    # that close the graph (they work on the budget's last sweep only: every other sweep
-    # is decided by its odd part here); the library picks the graph lengths (16, 8, 4,
-    # 2 or 1 sweeps) from the sweeps left as below
-    captured, replays, left = 0, 0, args.steps
-    while left > 0:
-        k = 0
-        while k < 4 and (16 >> (k + 1)) >= left:
-            k += 1
-        if (16 >> k) - left > 2 and k < 4:
-            k += 1
-        captured += 16 >> k
-        replays += 1
-        left -= 16 >> k
-    launches = 4 + captured * 3 + 2 * replays
+    launches = timed_fix_launches(args.steps)
 
     # ---- end to end through the C ABI with pinned host buffers: upload, one step, download
     Uh = torch.from_numpy(U).pin_memory()

@@ -35,3 +35,16 @@ def test_reference_arm_prints_one_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1"}) == []
+
+
+def test_timed_fix_launch_count():
+    # The launch count the bench line reports for its timed gf_fix: 68 kernels for the
+    # 20-step call, as ncu's launch list of that call counted them (launches 79-146 of the
+    # run summarised under profiles/); 200 and 4000 steps as the bench lines reported.
+    import bench
+    assert bench.timed_fix_launches(20) == 68
+    assert bench.timed_fix_launches(200) == 630
+    assert bench.timed_fix_launches(4000) == 12504
+    # short budgets: the graph that fits, at most two gated sweeps past the budget
+    assert bench.timed_fix_launches(1) == 4 + 3 + 2
+    assert bench.timed_fix_launches(3) == 4 + 3 * 4 + 2
